@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the bulk RSA-exponentiation generator on GB300.
+
+Workload (default): plain bulk, 1024 independent instances (seeded 32-bit
+prime pairs, e uniform over valid odd values in [3, 65537]), 2^20 float64
+outputs per instance per step, one instance per block: 2^30 numbers and
+8 GiB of output per step (larger than L2, so no flush is needed).
+
+A step is one pass of the whole hot path over the batch: skip update, message
+prefix, encryption, division and store for every output, plus the state
+write-back. `value` is Gnumbers/s with the instance table resident on the
+device; `e2e` is the same through the C ABI with host output buffers
+(rsaprng_generate_batch_host), device->host copies inside the timed region.
+
+`--impl reference` times the CPU oracle (the paper's CRT + Schrage route, OpenMP
+over instances) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): each rank owns its own 1024 instances (weak scaling, no
+data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workload  # noqa: E402
+
+METRIC = "Gnumbers/s float64 on 1 GB300, % int-pipe/HBM roofline; served p50/p99 latency"
+UNIT = "Gnumbers/s"
+WORKLOAD = "bulk_1024x2^20"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self, backend_gpu: bool):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("nccl" if backend_gpu else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def rank_seeds(cfg: dict, rank: int) -> np.ndarray:
+    """Per-rank instance seeds: rank r owns instances [r k, (r+1) k) of the master stream."""
+    k = cfg["instances"]
+    return workload.instance_seeds(cfg["master"], k, first=rank * k)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4)
+                          if r[5 + j].lower().startswith("active")})
+        # samples under load: the top half of the clock readings taken while busy
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- roofline
+def mul_instr_per_number(e: int) -> int:
+    """32-bit integer multiply instructions the CRT route needs per output.
+
+    Per prime: REDC of m (2), then (bitlen(e)-1) squarings, (popcount(e)-1)
+    multiplies and one correction, each a Montgomery product of 3 multiplies
+    (widening a*b, low m*pinv, high mq*p). Garner: one Montgomery product (3)
+    and the widening h*q (1). Skip a*s mod Q: 2 widening + 1. Integer
+    division: the 64x64->128 reciprocal product (4 widening + 2) and the low
+    64-bit product q*d (3).
+    """
+    b, w = e.bit_length(), bin(e).count("1")
+    per_prime = 2 + 3 * ((b - 1) + (w - 1) + 1)
+    return 2 * per_prime + 4 + 3 + 9
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except ValueError:
+            pass
+    return {}
+
+
+# --------------------------------------------------------------------------- CPU baseline
+def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
+    """The oracle (paper route: Schrage + CRT, OpenMP over instances) on a bounded sample."""
+    import oracle
+
+    oracle.build()
+    threads = oracle.max_threads()
+    k = min(len(seeds), max(threads * 4, 64))
+    par = [oracle.params_from_seed(int(s), cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+           for s in seeds[:k]]
+    p = np.array([x[0] for x in par], np.uint64)
+    q = np.array([x[1] for x in par], np.uint64)
+    e = np.array([x[2] for x in par], np.uint64)
+    a = np.full(k, 2307085864, np.uint64)
+
+    def run(n):
+        m = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
+        s = np.ones(k, np.uint64)
+        t0 = time.perf_counter()
+        oracle.generate_many(p, q, e, a, m, s, np.full(k, n, np.uint64),
+                             route=oracle.ROUTE_PAPER, want_c=False, want_r=True)
+        return time.perf_counter() - t0
+
+    pilot_n = 2048
+    dt = run(pilot_n)
+    n = int(min(cfg["count"], max(pilot_n, pilot_n * target_s / max(dt, 1e-3))))
+    dt = run(n)
+    return {"value": k * n / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {k} of {len(seeds)} instances x {n} numbers (of {cfg['count']}), "
+                      f"route=paper (Schrage + CRT), {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args) -> int:
+    import torch
+
+    import paper_1811_11629_gb300 as R
+
+    dist = Dist(backend_gpu=True)
+    torch.cuda.set_device(dist.local_rank)
+    cfg = workload.CONFIGS[WORKLOAD]
+    k, n = cfg["instances"], cfg["count"]
+    seeds = rank_seeds(cfg, dist.rank)
+    ctx = R.Context(k, device=dist.local_rank, chunk=n)
+    first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    ids = np.arange(first, first + k, dtype=np.uint32)
+    counts = np.full(k, n, np.uint64)
+    es = [ctx.params(int(i))[2] for i in ids]
+    tuned = None
+    if args.tune:
+        tuned = ctx.autotune(ids, counts, reps=1)
+    plan = ctx.plan(ids, counts)
+    out = torch.empty(k * n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.launch(out_r=out, stream=stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    launches0 = ctx.launches
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        plan.launch(out_r=out, stream=stream)
+        b.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    gpu_launches = ctx.launches - launches0
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed_max = dist.max(elapsed)
+    numbers_per_step = k * n
+    total_numbers = dist.sum(float(numbers_per_step * args.steps))
+    value = total_numbers / elapsed_max / 1e9
+
+    # Roofline of the generation kernel (one launch per step, plus a 4-byte ticket reset).
+    kern_s = statistics.mean(step_ms) / 1e3
+    ops = sum(mul_instr_per_number(int(e)) for e in es) * n
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak_alu = 152 * 64 * sm_max * 1e6 / 1e9  # G multiply lane-ops/s: 152 SMs x 64 lanes/clk
+    achieved = ops / kern_s / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    hbm_achieved = numbers_per_step * 8 / kern_s / 1e9
+
+    result = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_max * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": k, "numbers_per_instance": n,
+                   "e": "uniform over valid odd values in [3, 65537]", "output": "float64",
+                   "one_instance_per_block": True, "parallelism": f"instances x{dist.world}",
+                   "l2": "outputs 8 GiB per step > L2: no flush"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
+                     "unit": "Gop/s", "frac": round(achieved / peak_alu, 4), "traffic": None,
+                     "op": "32-bit integer multiply instruction (IMAD/IMAD.HI/IMAD.WIDE) per lane",
+                     "ops_per_step": ops, "peak_source": "152 SMs x 64 IMAD lanes/clk x sm_max",
+                     "kernel_ms": round(kern_s * 1e3, 3),
+                     "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak,
+                             "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4),
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks.get("hbm_gbs")
+                             else "fallback"}},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    if tuned:
+        result["config"]["tuned"] = {x: tuned[x] for x in ("modexp", "divide",
+                                                           "threads_per_block",
+                                                           "numbers_per_thread")}
+    cur = ctx.config()
+    result["config"]["kernel"] = {x: cur[x] for x in ("modexp", "divide", "threads_per_block",
+                                                      "numbers_per_thread")}
+    del out
+    torch.cuda.empty_cache()
+
+    if not args.no_e2e:
+        # End to end: the C-ABI call with a pinned host output buffer; the copies of
+        # 8 GiB per step to the host are inside the timed region.
+        h_out = torch.empty(k * n, dtype=torch.float64, pin_memory=True)
+        ctx.generate_batch_host(ids, counts, h_r=h_out)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.generate_batch_host(ids, counts, h_r=h_out)
+        dt = dist.max(time.perf_counter() - t0)
+        result["e2e"] = {"value": round(total_numbers / dt / 1e9, 4), "unit": UNIT,
+                         "h2d_bytes_per_step": k * 40 + 256,
+                         "d2h_bytes_per_step": numbers_per_step * 8}
+        del h_out
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(cfg, seeds)
+    if dist.rank == 0:
+        print(json.dumps(result), flush=True)
+    plan.close()
+    ctx.close()
+    dist.close()
+    return 0
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args) -> int:
+    """The oracle on the host cores, on the same workload, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cfg = workload.CONFIGS[WORKLOAD]
+    seeds = rank_seeds(cfg, 0)
+    threads = oracle.max_threads()
+    k = min(cfg["instances"], max(threads * 4, 64))
+    par = [oracle.params_from_seed(int(s), cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+           for s in seeds[:k]]
+    p = np.array([x[0] for x in par], np.uint64)
+    q = np.array([x[1] for x in par], np.uint64)
+    e = np.array([x[2] for x in par], np.uint64)
+    a = np.full(k, 2307085864, np.uint64)
+    m = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
+    s = np.ones(k, np.uint64)
+    per_step = 1 << 13  # numbers per instance per step (bounded sample)
+
+    def step():
+        oracle.generate_many(p, q, e, a, m, s, np.full(k, per_step, np.uint64),
+                             route=oracle.ROUTE_PAPER, want_c=False, want_r=True)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = k * per_step * args.steps / dt / 1e9
+    sample = (f"first {k} of {cfg['instances']} instances x {per_step} numbers per step "
+              f"(of {cfg['count']}), route=paper (Schrage + CRT)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": cfg["instances"],
+                   "numbers_per_instance": cfg["count"], "output": "float64"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def main(argv=None) -> int:
+    args = parse_args(argv)
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("--steps must be >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

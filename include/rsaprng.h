@@ -1,0 +1,298 @@
+/*
+ * rsaprng.h -- C ABI of the GB300 bulk generator for the RSA-exponentiation
+ * pseudorandom number generator of Datephanyawat & Beale (arXiv:1811.11629).
+ *
+ * What is computed (Sec. IV-V, Eq. algorithm1). An instance has fixed
+ * parameters {p, q, n = p q, e, Q = 2^63 - 25, a} and a state {m, s}. Each
+ * output k = 1, 2, ... advances the state and emits
+ *     s_k = a s_{k-1} mod Q                 (Eq. congruentialgenerator1)
+ *     m_k = (m_{k-1} + s_k) mod n           (Sec. IV message update)
+ *     c_k = m_k^e mod n                     (Eq. encrypt2)
+ *     r_k = RN(RN(c_k) / RN(n)), and 1 - 2^-53 in place of 1.0 (Sec. V)
+ * where RN is IEEE-754 round-to-nearest-even to double. All integer steps
+ * are exact; r_k is the C expression (double)c_k / (double)n.
+ *
+ * Parameters: p, q distinct primes in [2^31, 2^32) (Sec. V: 32-bit primes);
+ * e odd, 3 <= e < 2^32, gcd(e, (p-1)(q-1)) = 1 (Sec. III); a one of the
+ * restricted primitive roots mod Q listed below (Sec. V and its notes).
+ *
+ * Conventions for every call:
+ *  - Return value: RSAPRNG_OK (0) or a negative RSAPRNG_ERR_* code.
+ *    rsaprng_strerror() names it; rsaprng_last_error_detail() gives a
+ *    thread-local sentence about the last failure.
+ *  - Device pointers ("d_" prefix) are CUDA device addresses on the
+ *    context's device, owned by the caller; the library never frees them.
+ *    Host pointers ("h_" prefix or plain arrays) are read during the call
+ *    only (unless a function says otherwise).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Generation is asynchronous on that stream; instance state
+ *    advances in stream order, so calls for one instance must be ordered
+ *    (one stream, or events). Calls on different streams that touch the same
+ *    instance race.
+ *  - A context is not thread-safe; one host thread drives it at a time
+ *    (the server object has its own lock).
+ */
+#ifndef RSAPRNG_H
+#define RSAPRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define RSAPRNG_OK 0
+#define RSAPRNG_ERR_ARG (-1)         /* bad pointer, size or enum value */
+#define RSAPRNG_ERR_NOT_PRIME (-2)   /* p or q failed Rabin-Miller (Sec. V) */
+#define RSAPRNG_ERR_RANGE (-3)       /* p or q outside [2^31, 2^32) */
+#define RSAPRNG_ERR_P_EQ_Q (-4)      /* p == q */
+#define RSAPRNG_ERR_E (-5)           /* e even, < 3, or gcd(e,(p-1)(q-1)) != 1 */
+#define RSAPRNG_ERR_ROOT (-6)        /* a is not one of the allowed roots */
+#define RSAPRNG_ERR_OOM (-7)         /* device or host allocation failed */
+#define RSAPRNG_ERR_BUDGET (-8)      /* request larger than the server budget */
+#define RSAPRNG_ERR_CUDA (-9)        /* a CUDA runtime call failed */
+#define RSAPRNG_ERR_TIMEOUT (-10)    /* a host wait ran out of time */
+#define RSAPRNG_ERR_DEVICE_FLAG (-11)/* a kernel raised its error flag */
+#define RSAPRNG_ERR_CAPACITY (-12)   /* instance table full */
+#define RSAPRNG_ERR_CANCELLED (-13)  /* server request was cancelled */
+#define RSAPRNG_ERR_STATE (-14)      /* state (m, s) outside [0,n) x [1,Q-1] */
+#define RSAPRNG_ERR_ID (-15)         /* unknown instance id / ticket */
+#define RSAPRNG_ERR_BUSY (-16)       /* server queue full, try again */
+
+/* Q = 2^63 - 25, the skip modulus (Sec. V). */
+#define RSAPRNG_Q 0x7FFFFFFFFFFFFFE7ULL
+/* Default skip multiplier: the primitive root recommended by L'Ecuyer,
+ * Blouin & Couture (paper's reference note on that work). */
+#define RSAPRNG_DEFAULT_ROOT 2307085864ULL
+
+typedef struct rsaprng_ctx rsaprng_ctx;
+typedef struct rsaprng_server rsaprng_server;
+typedef struct rsaprng_plan rsaprng_plan;
+typedef uint32_t rsaprng_id;
+
+/* Encryption routes (both give bit-identical c_k). */
+enum {
+    RSAPRNG_MODEXP_AUTO = 0,
+    RSAPRNG_MODEXP_CRT32 = 1,  /* CRT + Garner (Eq. CRTimplementation), two
+                                  32-bit Montgomery exponentiations */
+    RSAPRNG_MODEXP_MONT64 = 2  /* one 64-bit Montgomery exponentiation mod n */
+};
+/* Division routes for r_k (both give bit-identical r_k). */
+enum {
+    RSAPRNG_DIVIDE_AUTO = 0,
+    RSAPRNG_DIVIDE_INT = 1,   /* integer rounding + division by the invariant
+                                 significand of RN(n) (Moller & Granlund 2011) */
+    RSAPRNG_DIVIDE_FP64 = 2   /* IEEE double conversion and division */
+};
+/* Exponent rules for rsaprng_params_from_seed. */
+enum { RSAPRNG_E_SMALLEST = 0, RSAPRNG_E_UNIFORM = 1, RSAPRNG_E_AT_LEAST = 2 };
+
+/* Tuning knobs; zero fields mean "use the tuned/default value". */
+typedef struct {
+    uint32_t struct_size;       /* sizeof(rsaprng_config) */
+    int32_t modexp;             /* RSAPRNG_MODEXP_* */
+    int32_t divide;             /* RSAPRNG_DIVIDE_* */
+    int32_t threads_per_block;  /* 128, 256, 512 or 1024 */
+    int32_t numbers_per_thread; /* 2, 4 or 8 */
+    int32_t blocks_per_sm;      /* persistent-launch occupancy target */
+    uint64_t chunk;             /* numbers per chunk of a long stream (multiple
+                                   of threads_per_block*numbers_per_thread) */
+    int32_t require_safe;       /* p, q must be safe primes (Sec. V) */
+    int32_t reserved[7];
+} rsaprng_config;
+
+/* ------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device` with room for `max_instances`
+ * instances (device table: 96 B parameters + 16 B state each). cfg may be
+ * NULL. Makes `device` current on the calling thread. */
+int rsaprng_ctx_create(rsaprng_ctx **out, int device, uint64_t max_instances,
+                       const rsaprng_config *cfg);
+void rsaprng_ctx_destroy(rsaprng_ctx *ctx);
+/* Replaces the tuning knobs (validated; zero fields keep defaults). */
+int rsaprng_ctx_configure(rsaprng_ctx *ctx, const rsaprng_config *cfg);
+int rsaprng_ctx_get_config(const rsaprng_ctx *ctx, rsaprng_config *out);
+uint64_t rsaprng_instance_count(const rsaprng_ctx *ctx);
+
+/* ----------------------------------------------------------- instances */
+
+/* One instance from {p, q, e} and a message seed (Sec. IV: "seeding is
+ * simple"): a = RSAPRNG_DEFAULT_ROOT, m_0 = seed mod n, s_0 = 1, so the first
+ * output uses m_1 = m_0 + a mod n. Validates p, q by trial division and
+ * deterministic Rabin-Miller (Sec. V). Synchronous host->device write. */
+int rsaprng_instance_create(rsaprng_ctx *ctx, uint64_t p, uint64_t q, uint64_t e, uint64_t seed,
+                            rsaprng_id *out);
+/* Explicit skip multiplier and start state: a must be an allowed root,
+ * m0 < n, 1 <= s0 < Q. */
+int rsaprng_instance_create_ex(rsaprng_ctx *ctx, uint64_t p, uint64_t q, uint64_t e, uint64_t a,
+                               uint64_t m0, uint64_t s0, rsaprng_id *out);
+/* `count` instances from host arrays (same rules as rsaprng_instance_create);
+ * ids are consecutive from *out_first. All or nothing: on error nothing is
+ * added and the index of the first bad entry is in the error detail. */
+int rsaprng_instances_create_bulk(rsaprng_ctx *ctx, uint64_t count, const uint64_t *p,
+                                  const uint64_t *q, const uint64_t *e, const uint64_t *seed,
+                                  rsaprng_id *out_first);
+/* `count` instances from 64-bit seeds by rsaprng_params_from_seed; uses all
+ * host cores. ids are consecutive from *out_first. */
+int rsaprng_instances_create_seeded(rsaprng_ctx *ctx, uint64_t count, const uint64_t *seeds,
+                                    int e_rule, uint64_t e_lo, uint64_t e_hi,
+                                    rsaprng_id *out_first);
+
+/* Stream splitting (Sec. VI): Mv children of `parent`, child gamma with the
+ * parent's parameters and current message, and skip
+ *     s^(gamma) = s * a^(gamma floor((Q-1)/Mv)) mod Q.
+ * Child 0 continues the parent's stream. The parent is unchanged. */
+int rsaprng_split(rsaprng_ctx *ctx, rsaprng_id parent, uint32_t Mv, rsaprng_id *out_children);
+
+/* Checkpoint / resume (Sec. IV: the state is {m, s}). Synchronous. */
+int rsaprng_get_state(rsaprng_ctx *ctx, rsaprng_id id, uint64_t *m, uint64_t *s);
+int rsaprng_set_state(rsaprng_ctx *ctx, rsaprng_id id, uint64_t m, uint64_t s);
+/* Fixed parameters of an instance (any output pointer may be NULL). */
+int rsaprng_get_params(rsaprng_ctx *ctx, rsaprng_id id, uint64_t *p, uint64_t *q, uint64_t *e,
+                       uint64_t *a);
+
+/* ---------------------------------------------------------- generation */
+
+/* N outputs of one instance into caller device buffers (Eq. algorithm1):
+ * d_c[k] = c_{k+1}, d_r[k] = r_{k+1}; advances the instance by N. Long
+ * streams are cut into chunks whose start states come from an on-device
+ * skip-sum pass, so the whole GPU works on one instance. */
+int rsaprng_generate_u64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, void *stream);
+int rsaprng_generate_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_r, void *stream);
+int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
+                          void *stream);
+
+/* Many requests in one launch sequence. Request i draws counts[i] outputs of
+ * instance ids[i] into d_r/d_c at element offset out_offsets[i] (either
+ * output may be NULL). ids, counts, out_offsets are HOST arrays. Requests of
+ * the same instance are served in array order (each continues after the
+ * previous one). */
+int rsaprng_generate_batch(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                           const uint64_t *counts, const uint64_t *out_offsets, double *d_r,
+                           uint64_t *d_c, void *stream);
+
+/* The same with HOST output buffers (end to end): the library copies the
+ * outputs device->host itself, overlapping copies with generation, and
+ * returns when h_r / h_c hold the results. Either may be NULL. Pinned host
+ * memory is fastest. */
+int rsaprng_generate_batch_host(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                                const uint64_t *counts, const uint64_t *out_offsets, double *h_r,
+                                uint64_t *h_c, void *stream);
+
+/* ------------------------------------------------ plans and CUDA graphs */
+
+/* A device-resident launch plan for a fixed set of requests (same meaning
+ * as rsaprng_generate_batch). Launching it generates the next outputs of the
+ * requests each time. rsaprng_plan_capture records the launches into a CUDA
+ * graph bound to the given output buffers; rsaprng_plan_replay launches that
+ * graph. */
+int rsaprng_plan_create(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                        const uint64_t *counts, const uint64_t *out_offsets, rsaprng_plan **out);
+int rsaprng_plan_launch(rsaprng_plan *plan, double *d_r, uint64_t *d_c, void *stream);
+int rsaprng_plan_capture(rsaprng_plan *plan, double *d_r, uint64_t *d_c, void *stream);
+int rsaprng_plan_replay(rsaprng_plan *plan, void *stream);
+/* Kernel launches one rsaprng_plan_launch makes, and numbers it generates. */
+int rsaprng_plan_info(const rsaprng_plan *plan, uint64_t *launches, uint64_t *numbers,
+                      uint64_t *chunks);
+void rsaprng_plan_destroy(rsaprng_plan *plan);
+
+/* --------------------------------------------------------------- tuning */
+
+/* Times the candidate tilings and routes on a plan built from the given
+ * requests (outputs go to scratch buffers the call allocates and frees) and
+ * stores the fastest in the context's config. Every candidate gives
+ * bit-identical outputs. */
+int rsaprng_autotune(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                     const uint64_t *counts, int reps, rsaprng_config *chosen);
+
+/* -------------------------------------------------------------- serving */
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected, cancelled;
+    uint64_t queued_now, inflight_now;
+    uint64_t numbers_done;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* arrival -> completion latency */
+    double busy_s, wall_s;                  /* device-busy and wall time */
+    uint64_t iterations;                    /* batched launches issued */
+} rsaprng_stats;
+
+/* A continuous-batching request server over the context's instances. It owns
+ * an output arena of `out_budget_bytes` device bytes: a request is admitted
+ * when its 8 B/number fit in the arena, otherwise it waits in FIFO order.
+ * Each server iteration gathers admitted work (large requests in chunks),
+ * launches one batched pass on one of `nstreams` streams, and releases arena
+ * space when the client calls rsaprng_server_release. */
+int rsaprng_server_create(rsaprng_ctx *ctx, uint64_t out_budget_bytes, int nstreams,
+                          rsaprng_server **out);
+/* Queues `count` float64 outputs of instance `id`. The result is the
+ * instance's next `count` outputs at the time of admission order. */
+int rsaprng_server_submit(rsaprng_server *srv, rsaprng_id id, uint64_t count, uint64_t *ticket);
+/* *done = 1 when the ticket's outputs are complete on the device. */
+int rsaprng_server_poll(rsaprng_server *srv, uint64_t ticket, int *done);
+/* Waits up to timeout_ns for the ticket (RSAPRNG_ERR_TIMEOUT otherwise). */
+int rsaprng_server_wait(rsaprng_server *srv, uint64_t ticket, uint64_t timeout_ns);
+/* Device address of a completed ticket's outputs (valid until released). */
+int rsaprng_server_result(rsaprng_server *srv, uint64_t ticket, const double **d_r,
+                          uint64_t *count);
+/* Copies a completed ticket's outputs to d_dst (count doubles) on `stream`. */
+int rsaprng_server_copy(rsaprng_server *srv, uint64_t ticket, double *d_dst, void *stream);
+int rsaprng_server_release(rsaprng_server *srv, uint64_t ticket);
+/* Cancels a ticket that has not been admitted yet. */
+int rsaprng_server_cancel(rsaprng_server *srv, uint64_t ticket);
+int rsaprng_server_stats(rsaprng_server *srv, rsaprng_stats *out);
+void rsaprng_server_destroy(rsaprng_server *srv);
+
+/* ------------------------------------------------------- host utilities */
+
+/* Deterministic primality of a 64-bit integer: trial division by small
+ * primes, then Rabin-Miller with bases {2,3,5,7,11} below 2^32 and the
+ * twelve smallest primes below 2^64 (Sec. V). Returns 1 or 0. */
+int rsaprng_is_prime(uint64_t x);
+/* Validates instance parameters without creating an instance: returns
+ * RSAPRNG_OK or the code rsaprng_instance_create would return (RANGE,
+ * P_EQ_Q, NOT_PRIME, E). require_safe adds the safe-prime rule of Sec. V. */
+int rsaprng_validate_params(uint64_t p, uint64_t q, uint64_t e, int require_safe);
+/* 1 if a is allowed as a skip multiplier: the recommended root, the eight
+ * listed roots of Sezgin & Sezgin that are primitive (3163786287 is not: it
+ * is a quadratic residue mod Q), or one of the five smallest primitive roots
+ * {3, 6, 7, 10, 11} used for the weakened-generator tests (Sec. VII). */
+int rsaprng_root_allowed(uint64_t a);
+
+/* Instance parameters from one 64-bit seed (the rule the workloads use; it
+ * is not from the paper). Draws x_1, x_2, ... come from SplitMix64 (Steele,
+ * Lea & Flood 2014) started at `seed`. A prime candidate is (x >> 32) |
+ * 0x80000001. p is the first prime candidate, q the next prime candidate
+ * != p. e by rule: SMALLEST = smallest odd e >= 3 with gcd(e, phi) = 1;
+ * AT_LEAST = smallest such odd e >= e_lo; UNIFORM = draws
+ * e = e_lo + 2 (x mod ((e_hi - e_lo)/2 + 1)) until gcd(e, phi) = 1 (e_lo odd).
+ * The message seed is the next draw. */
+int rsaprng_params_from_seed(uint64_t seed, int e_rule, uint64_t e_lo, uint64_t e_hi,
+                             uint64_t *p, uint64_t *q, uint64_t *e, uint64_t *msg_seed);
+
+/* The output step alone (Eq. CodeFloatingPointStep with the Sec. V guard):
+ * d_r[k] = RN(RN(d_c[k]) / RN(n_id)), 1 - 2^-53 in place of 1.0, for k < N,
+ * using division route `divide` (RSAPRNG_DIVIDE_*; AUTO = the context's).
+ * d_c values must be < n of instance `id`. Asynchronous on `stream`. */
+int rsaprng_unit_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, const uint64_t *d_c,
+                     double *d_r, int divide, void *stream);
+
+/* Kernel launches issued by this context so far (for launch accounting). */
+uint64_t rsaprng_launch_count(const rsaprng_ctx *ctx);
+
+/* ----------------------------------------------------- microbenchmarks */
+
+/* Device microbenchmarks for the roofline, timed with CUDA events on an
+ * internal stream: kind 0 = 32-bit integer multiply-add issue rate
+ * (result in G lane-ops/s), 1 = FP64 divide rate (G div/s), 2 = HBM write
+ * bandwidth (GB/s) over `bytes` bytes. */
+int rsaprng_microbench(rsaprng_ctx *ctx, int kind, uint64_t bytes, double *result);
+
+const char *rsaprng_strerror(int code);
+const char *rsaprng_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSAPRNG_H */

@@ -72,6 +72,11 @@ def lib():
                 "or_crt_encrypt": (u64, [u64, u64, u64, u64, u64, u64]),
                 "or_unit": (dbl, [u64, u64]),
                 "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
+                "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
+                "or_sample": (i32, [ctypes.c_void_p, pu64, pu64, pu64, u64, pu64, pdbl]),
+                "or_sample_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64,
+                                         pu64, pu64, pu64, pdbl]),
+                "or_unit_many": (None, [pu64, u64, pdbl, u64]),
                 "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
                                            pu64, pu64, pu64, pdbl, i32]),
                 "or_max_threads": (i32, []),
@@ -199,6 +204,47 @@ def generate(p, q, e, m0, s0, count, a=2307085864, q_mod=Q, route=ROUTE_CHECKED,
     if rc != 0:
         raise RuntimeError(f"oracle generate failed ({rc})")
     return c, r, m.value, s.value
+
+
+def seek(p, q, a, m0, s0, k, q_mod=Q):
+    """State after k outputs from (m0, s0), without encryption (Sec. IV sums)."""
+    P = _Params(p, q, 3, a, q_mod)
+    m = ctypes.c_uint64(m0)
+    s = ctypes.c_uint64(s0)
+    rc = lib().or_seek(ctypes.byref(P), ctypes.byref(m), ctypes.byref(s), k)
+    if rc != 0:
+        raise RuntimeError(f"oracle seek failed ({rc})")
+    return m.value, s.value
+
+
+def sample_many(p, q, e, a, m, s, ks_list, q_mod=Q):
+    """Sampled outputs of many instances; ks_list[i] = increasing 1-based indices.
+
+    m, s (uint64 arrays) are advanced in place to each instance's last sample.
+    Returns (c, r) concatenated in instance order.
+    """
+    p, q, e, a = (np.ascontiguousarray(x, dtype=np.uint64) for x in (p, q, e, a))
+    nk = np.array([len(k) for k in ks_list], dtype=np.uint64)
+    koff = np.zeros_like(nk)
+    if len(nk) > 1:
+        koff[1:] = np.cumsum(nk[:-1], dtype=np.uint64)
+    ks = np.ascontiguousarray(np.concatenate([np.asarray(k, dtype=np.uint64) for k in ks_list])
+                              if len(ks_list) else np.zeros(0, np.uint64))
+    c = np.empty(len(ks), np.uint64)
+    r = np.empty(len(ks), np.float64)
+    rc = lib().or_sample_many(len(nk), _p64(p), _p64(q), _p64(e), _p64(a), q_mod, _p64(m),
+                              _p64(s), _p64(ks), _p64(koff), _p64(nk), _p64(c), _pd(r))
+    if rc != 0:
+        raise RuntimeError(f"oracle sample_many failed ({rc})")
+    return c, r
+
+
+def unit_many(c: np.ndarray, n: int) -> np.ndarray:
+    """or_unit over an array (Eq. CodeFloatingPointStep)."""
+    c = np.ascontiguousarray(c, dtype=np.uint64)
+    r = np.empty(len(c), np.float64)
+    lib().or_unit_many(_p64(c), n, _pd(r), len(c))
+    return r
 
 
 def generate_many(p, q, e, a, m, s, counts, offsets=None, route=ROUTE_CHECKED, want_c=True,

@@ -349,6 +349,82 @@ int or_generate(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t N,
 }
 
 /*
+ * Advances the state by k outputs without encrypting: k steps of
+ * s <- a s mod Q, m <- (m + s) mod n (Sec. IV). This is the summation of
+ * Eq. pseudoskip carried out term by term.
+ */
+int or_seek(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t k)
+{
+    const uint64_t n = P->p * P->q;
+    uint64_t m = *m_io, s = *s_io;
+    if (m >= n || s == 0 || s >= P->Q)
+        return OR_ERR_ARG;
+    for (uint64_t i = 0; i < k; i++) {
+        s = or_skip_next_direct(s, P->a, P->Q);
+        m = or_addmod(m, s % n, n);
+    }
+    *m_io = m;
+    *s_io = s;
+    return OR_OK;
+}
+
+/*
+ * Sampled outputs of one instance: for the increasing 1-based output indices
+ * ks[0] < ks[1] < ... < ks[nk-1], c_out[j] / r_out[j] receive c_k, r_k with
+ * k = ks[j]. The state is advanced by Sec. IV's sums (or_seek) between the
+ * samples and each sample is encrypted by the direct route. (*m_io, *s_io)
+ * end at output ks[nk-1].
+ */
+int or_sample(const or_params *P, uint64_t *m_io, uint64_t *s_io, const uint64_t *ks,
+              uint64_t nk, uint64_t *c_out, double *r_out)
+{
+    const uint64_t n = P->p * P->q;
+    uint64_t done = 0;
+    for (uint64_t j = 0; j < nk; j++) {
+        if (ks[j] <= done)
+            return OR_ERR_ARG;
+        int rc = or_seek(P, m_io, s_io, ks[j] - done);
+        if (rc != OR_OK)
+            return rc;
+        done = ks[j];
+        uint64_t c = or_encrypt_direct(*m_io, P->e, n);
+        if (c_out)
+            c_out[j] = c;
+        if (r_out)
+            r_out[j] = or_unit(c, n);
+    }
+    return OR_OK;
+}
+
+/* or_sample over many instances in parallel: instance i samples the nk[i]
+ * indices at ks + koff[i] and writes at c_out/r_out + koff[i]. */
+int or_sample_many(uint64_t count, const uint64_t *p, const uint64_t *q, const uint64_t *e,
+                   const uint64_t *a, uint64_t Q, uint64_t *m, uint64_t *s, const uint64_t *ks,
+                   const uint64_t *koff, const uint64_t *nk, uint64_t *c_out, double *r_out)
+{
+    int err = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < (int64_t)count; i++) {
+        or_params P = {p[i], q[i], e[i], a[i], Q};
+        int rc = or_sample(&P, &m[i], &s[i], ks + koff[i], nk[i], c_out ? c_out + koff[i] : NULL,
+                           r_out ? r_out + koff[i] : NULL);
+        if (rc != OR_OK) {
+#pragma omp critical
+            if (err == OR_OK)
+                err = rc;
+        }
+    }
+    return err;
+}
+
+/* r[i] = or_unit(c[i], n) for i < count. */
+void or_unit_many(const uint64_t *c, uint64_t n, double *r, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; i++)
+        r[i] = or_unit(c[i], n);
+}
+
+/*
  * Many independent instances (parameterization, Sec. VI), one output region
  * per instance: instance i writes counts[i] values at offsets[i] of c_out /
  * r_out (either may be NULL) and has its state (m[i], s[i]) advanced.

@@ -1,0 +1,827 @@
+// Host runtime and C ABI of the generator library (declarations and the
+// meaning of every call are in include/rsaprng.h).
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rsaprng.h"
+#include "api_internal.hpp"
+#include "host_params.hpp"
+#include "kernels.cuh"
+
+using namespace rsaprng;
+
+namespace rsaprng {
+
+thread_local std::string g_detail;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_detail = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(RSAPRNG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static const rsaprng_config kDefaultConfig = {
+    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT, 256, 4, 0, 1ULL << 18, 0,
+    {0, 0, 0, 0, 0, 0, 0}};
+
+static int check_config(const rsaprng_config &c)
+{
+    if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 2)
+        return fail(RSAPRNG_ERR_ARG, "config: modexp/divide out of range");
+    if (c.threads_per_block && c.threads_per_block != 128 && c.threads_per_block != 256 &&
+        c.threads_per_block != 512)
+        return fail(RSAPRNG_ERR_ARG, "config: threads_per_block must be 128, 256 or 512");
+    if (c.numbers_per_thread && c.numbers_per_thread != 2 && c.numbers_per_thread != 4 &&
+        c.numbers_per_thread != 8)
+        return fail(RSAPRNG_ERR_ARG, "config: numbers_per_thread must be 2, 4 or 8");
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32)
+        return fail(RSAPRNG_ERR_ARG, "config: blocks_per_sm out of range");
+    return RSAPRNG_OK;
+}
+
+static rsaprng_config merged(const rsaprng_config &base, const rsaprng_config *over)
+{
+    rsaprng_config c = base;
+    if (!over)
+        return c;
+    if (over->modexp)
+        c.modexp = over->modexp;
+    if (over->divide)
+        c.divide = over->divide;
+    if (over->threads_per_block)
+        c.threads_per_block = over->threads_per_block;
+    if (over->numbers_per_thread)
+        c.numbers_per_thread = over->numbers_per_thread;
+    if (over->blocks_per_sm)
+        c.blocks_per_sm = over->blocks_per_sm;
+    if (over->chunk)
+        c.chunk = over->chunk;
+    c.require_safe = over->require_safe;
+    return c;
+}
+
+DeviceTables ctx_tables(rsaprng_ctx *c)
+{
+    DeviceTables t;
+    t.params = c->d_params;
+    t.state_m = c->d_m;
+    t.state_s = c->d_s;
+    t.pow_lin = c->d_pow_lin;
+    t.pow2k = c->d_pow2k;
+    return t;
+}
+
+GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
+                     bool want_c)
+{
+    GenLaunch g;
+    g.threads = cfg.threads_per_block;
+    g.L = cfg.numbers_per_thread;
+    g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
+    g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64 : DIVIDE_INT;
+    const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
+    int occ = gen_blocks_per_sm(g, smem);
+    if (occ < 1)
+        occ = 1;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ)
+        occ = cfg.blocks_per_sm;
+    const uint64_t resident = (uint64_t)occ * c->sms;
+    if (nitems <= resident) {
+        g.grid = (int)std::max<uint64_t>(nitems, 1);
+        g.persistent = false;
+    } else {
+        g.grid = (int)resident;
+        g.persistent = true;
+    }
+    return g;
+}
+
+// Cost of one output in Montgomery-product units: squarings + multiplies of
+// the exponent chain plus a fixed share for the skip, scan and division.
+static inline uint64_t cost_per_number(uint32_t e)
+{
+    const int bl = 32 - __builtin_clz(e);
+    return (uint64_t)(bl + __builtin_popcount(e) + 6);
+}
+
+int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
+               const uint64_t *offsets, uint64_t chunk, HostPlan &hp)
+{
+    hp.items.clear();
+    hp.chunks.clear();
+    hp.groups.clear();
+    hp.numbers = 0;
+    if (chunk == 0)
+        chunk = ~0ULL;
+    // Group requests by instance, keeping array order inside each instance.
+    std::vector<uint64_t> order(nreq);
+    for (uint64_t i = 0; i < nreq; i++) {
+        if (ids[i] >= c->count)
+            return fail(RSAPRNG_ERR_ID, "request %llu: unknown instance id %u",
+                        (unsigned long long)i, ids[i]);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint64_t x, uint64_t y) { return ids[x] < ids[y]; });
+    struct Piece {
+        uint64_t offset, len, out;
+    };
+    std::vector<Piece> pieces;
+    std::vector<uint64_t> item_cost;
+    for (uint64_t g0 = 0; g0 < nreq;) {
+        uint64_t g1 = g0;
+        const rsaprng_id id = ids[order[g0]];
+        while (g1 < nreq && ids[order[g1]] == id)
+            g1++;
+        pieces.clear();
+        uint64_t off = 0;
+        for (uint64_t k = g0; k < g1; k++) {
+            const uint64_t r = order[k];
+            uint64_t left = counts[r], out = offsets[r];
+            while (left > 0) {
+                const uint64_t room = chunk - (off % chunk);
+                const uint64_t len = std::min(left, room);
+                pieces.push_back({off, len, out});
+                off += len;
+                out += len;
+                left -= len;
+            }
+        }
+        g0 = g1;
+        if (pieces.empty())
+            continue;
+        hp.numbers += off;
+        const uint64_t w = cost_per_number(c->h_params[id].e);
+        if (pieces.size() == 1) {
+            WorkItem it{id, WI_FROM_STATE | WI_WRITEBACK, pieces[0].len, pieces[0].out, 0, 0};
+            hp.items.push_back(it);
+            item_cost.push_back(pieces[0].len * w);
+            continue;
+        }
+        PrepGroup grp{id, (uint32_t)hp.chunks.size(), (uint32_t)pieces.size(), 0};
+        hp.groups.push_back(grp);
+        for (size_t k = 0; k < pieces.size(); k++) {
+            const bool last = k + 1 == pieces.size();
+            WorkItem it{id, last ? (uint32_t)WI_WRITEBACK : 0u, pieces[k].len, pieces[k].out, 0, 0};
+            PrepChunk pc{id, (uint32_t)hp.items.size(), pieces[k].offset, pieces[k].len};
+            hp.chunks.push_back(pc);
+            hp.items.push_back(it);
+            item_cost.push_back(pieces[k].len * w);
+        }
+    }
+    if (hp.items.size() > 0xFFFFFFF0ULL || hp.chunks.size() > 0xFFFFFFF0ULL)
+        return fail(RSAPRNG_ERR_ARG, "plan too large");
+    // Longest-processing-time-first order for the persistent launch.
+    std::vector<uint32_t> perm(hp.items.size()), where(hp.items.size());
+    for (size_t i = 0; i < perm.size(); i++)
+        perm[i] = (uint32_t)i;
+    std::stable_sort(perm.begin(), perm.end(),
+                     [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
+    std::vector<WorkItem> sorted(hp.items.size());
+    for (size_t i = 0; i < perm.size(); i++) {
+        sorted[i] = hp.items[perm[i]];
+        where[perm[i]] = (uint32_t)i;
+    }
+    hp.items.swap(sorted);
+    for (auto &pc : hp.chunks)
+        pc.item = where[pc.item];
+    return RSAPRNG_OK;
+}
+
+static int grow(void **p, size_t *cap, size_t need)
+{
+    if (need <= *cap)
+        return RSAPRNG_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess)
+        return fail(RSAPRNG_ERR_OOM, "cudaMalloc(%zu): %s", n, cudaGetErrorString(e));
+    *cap = n;
+    return RSAPRNG_OK;
+}
+
+static int grow_host(void **p, size_t *cap, size_t need)
+{
+    if (need <= *cap)
+        return RSAPRNG_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*p)
+        cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMallocHost(p, n);
+    if (e != cudaSuccess)
+        return fail(RSAPRNG_ERR_OOM, "cudaMallocHost(%zu): %s", n, cudaGetErrorString(e));
+    *cap = n;
+    return RSAPRNG_OK;
+}
+
+// Uploads a host plan into device buffers (through pinned staging) and
+// records the launch layout. The buffers are reused; the caller guarantees
+// that no earlier launch using them is still pending.
+int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream)
+{
+    const size_t b_items = hp.items.size() * sizeof(WorkItem);
+    const size_t b_chunks = hp.chunks.size() * sizeof(PrepChunk);
+    const size_t b_groups = hp.groups.size() * sizeof(PrepGroup);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t total = al(b_items) + al(b_chunks) + al(b_groups) + 256;
+    int rc;
+    if ((rc = grow(&dp.d_buf, &dp.cap_buf, total)) != RSAPRNG_OK)
+        return rc;
+    if ((rc = grow_host(&dp.h_buf, &dp.cap_host, total)) != RSAPRNG_OK)
+        return rc;
+    const size_t b_sums = hp.chunks.size() * 8 * 2;
+    if ((rc = grow(&dp.d_sums, &dp.cap_sums, std::max<size_t>(b_sums, 256))) != RSAPRNG_OK)
+        return rc;
+    char *h = (char *)dp.h_buf;
+    char *d = (char *)dp.d_buf;
+    size_t o = 0;
+    dp.items = (WorkItem *)(d + o);
+    memcpy(h + o, hp.items.data(), b_items);
+    o += al(b_items);
+    dp.chunks = (PrepChunk *)(d + o);
+    memcpy(h + o, hp.chunks.data(), b_chunks);
+    o += al(b_chunks);
+    dp.groups = (PrepGroup *)(d + o);
+    memcpy(h + o, hp.groups.data(), b_groups);
+    o += al(b_groups);
+    dp.ticket = (uint32_t *)(d + o);
+    memset(h + o, 0, 256);
+    o += 256;
+    dp.chunk_sum = (uint64_t *)dp.d_sums;
+    dp.chunk_s = (uint64_t *)dp.d_sums + hp.chunks.size();
+    dp.nitems = (uint32_t)hp.items.size();
+    dp.nchunks = (uint32_t)hp.chunks.size();
+    dp.ngroups = (uint32_t)hp.groups.size();
+    dp.numbers = hp.numbers;
+    cudaError_t e = cudaMemcpyAsync(dp.d_buf, dp.h_buf, o, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "plan upload");
+    return RSAPRNG_OK;
+}
+
+int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
+                uint64_t *d_c, cudaStream_t stream, uint64_t *launches)
+{
+    const DeviceTables t = ctx_tables(c);
+    uint64_t nl = 0;
+    cudaError_t e;
+    if (dp.nchunks) {
+        if ((e = launch_prep_sums(t, dp.chunks, dp.nchunks, dp.chunk_sum, dp.chunk_s, stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "prep sums launch");
+        if ((e = launch_prep_scan(t, dp.groups, dp.ngroups, dp.chunks, dp.chunk_sum, dp.chunk_s,
+                                  dp.items, stream)) != cudaSuccess)
+            return cuda_fail(e, "prep scan launch");
+        nl += 2;
+    }
+    if (dp.nitems) {
+        GenLaunch g = ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr);
+        if (g.persistent) {
+            if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
+                return cuda_fail(e, "ticket reset");
+        }
+        if ((e = launch_generate(g, t, dp.items, dp.nitems, dp.ticket, d_r, d_c, stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "generate launch");
+        nl += 1;
+    }
+    c->launches += nl;
+    if (launches)
+        *launches = nl;
+    return RSAPRNG_OK;
+}
+
+void free_devplan(DevPlan &dp)
+{
+    if (dp.d_buf)
+        cudaFree(dp.d_buf);
+    if (dp.d_sums)
+        cudaFree(dp.d_sums);
+    if (dp.h_buf)
+        cudaFreeHost(dp.h_buf);
+    dp = DevPlan{};
+}
+
+// Scratch plan slots for one-off generate calls: slot k is reused only after
+// the event recorded behind its last launch has completed.
+int scratch_slot(rsaprng_ctx *c, ScratchSlot **out)
+{
+    ScratchSlot &s = c->slots[c->next_slot];
+    c->next_slot = (c->next_slot + 1) % kScratchSlots;
+    if (s.used) {
+        cudaError_t e = cudaEventSynchronize(s.done);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "scratch slot wait");
+    }
+    *out = &s;
+    return RSAPRNG_OK;
+}
+
+}  // namespace rsaprng
+
+namespace rsaprng {
+// Runs f(i) for i in [0, count) over all host cores.
+template <typename F>
+static void parallel_for(uint64_t count, F &&f)
+{
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if (count < 4096 || nt == 1) {
+        for (uint64_t i = 0; i < count; i++)
+            f(i);
+        return;
+    }
+    std::atomic<uint64_t> next{0};
+    std::vector<std::thread> th;
+    for (unsigned k = 0; k < nt; k++)
+        th.emplace_back([&] {
+            for (;;) {
+                uint64_t i0 = next.fetch_add(1024);
+                if (i0 >= count)
+                    break;
+                uint64_t i1 = std::min(count, i0 + 1024);
+                for (uint64_t i = i0; i < i1; i++)
+                    f(i);
+            }
+        });
+    for (auto &x : th)
+        x.join();
+}
+
+}  // namespace rsaprng
+
+// ============================================================ C ABI
+
+extern "C" {
+
+const char *rsaprng_strerror(int code)
+{
+    switch (code) {
+    case RSAPRNG_OK: return "ok";
+    case RSAPRNG_ERR_ARG: return "invalid argument";
+    case RSAPRNG_ERR_NOT_PRIME: return "p or q is not prime";
+    case RSAPRNG_ERR_RANGE: return "p or q outside [2^31, 2^32)";
+    case RSAPRNG_ERR_P_EQ_Q: return "p equals q";
+    case RSAPRNG_ERR_E: return "invalid exponent e";
+    case RSAPRNG_ERR_ROOT: return "skip multiplier is not an allowed primitive root";
+    case RSAPRNG_ERR_OOM: return "out of memory";
+    case RSAPRNG_ERR_BUDGET: return "request exceeds the output budget";
+    case RSAPRNG_ERR_CUDA: return "CUDA error";
+    case RSAPRNG_ERR_TIMEOUT: return "timed out";
+    case RSAPRNG_ERR_DEVICE_FLAG: return "device error flag raised";
+    case RSAPRNG_ERR_CAPACITY: return "instance table full";
+    case RSAPRNG_ERR_CANCELLED: return "request cancelled";
+    case RSAPRNG_ERR_STATE: return "state outside its range";
+    case RSAPRNG_ERR_ID: return "unknown id";
+    case RSAPRNG_ERR_BUSY: return "queue full";
+    default: return "unknown error";
+    }
+}
+
+const char *rsaprng_last_error_detail(void) { return g_detail.c_str(); }
+
+int rsaprng_is_prime(uint64_t x) { return rsaprng::is_prime(x) ? 1 : 0; }
+
+int rsaprng_root_allowed(uint64_t a) { return root_index(a) >= 0 ? 1 : 0; }
+
+int rsaprng_validate_params(uint64_t p, uint64_t q, uint64_t e, int require_safe)
+{
+    return validate_pqe(p, q, e, require_safe != 0);
+}
+
+int rsaprng_params_from_seed(uint64_t seed, int e_rule, uint64_t e_lo, uint64_t e_hi,
+                             uint64_t *p, uint64_t *q, uint64_t *e, uint64_t *msg_seed)
+{
+    if (!p || !q || !e || !msg_seed)
+        return fail(RSAPRNG_ERR_ARG, "null output pointer");
+    return rsaprng::params_from_seed(seed, e_rule, e_lo, e_hi, *p, *q, *e, *msg_seed);
+}
+
+int rsaprng_ctx_create(rsaprng_ctx **out, int device, uint64_t max_instances,
+                       const rsaprng_config *cfg)
+{
+    if (!out || max_instances == 0 || max_instances > 0xFFFFFFF0ULL)
+        return fail(RSAPRNG_ERR_ARG, "ctx_create: bad arguments");
+    *out = nullptr;
+    rsaprng_config conf = merged(kDefaultConfig, cfg);
+    int rc = check_config(conf);
+    if (rc)
+        return rc;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaSetDevice");
+    rsaprng_ctx *c = new (std::nothrow) rsaprng_ctx();
+    if (!c)
+        return fail(RSAPRNG_ERR_OOM, "ctx alloc");
+    c->device = device;
+    c->cfg = conf;
+    c->capacity = max_instances;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    auto cleanup = [&](int code) {
+        rsaprng_ctx_destroy(c);
+        return code;
+    };
+    if ((e = cudaMalloc(&c->d_params, max_instances * sizeof(InstParams))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_m, max_instances * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_s, max_instances * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_pow_lin, (size_t)kNumRoots * kPowLinRow * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_pow2k, (size_t)kNumRoots * 64 * 8)) != cudaSuccess)
+        return cleanup(fail(RSAPRNG_ERR_OOM, "device tables: %s", cudaGetErrorString(e)));
+    // Power tables of every allowed root: a^i (i <= kMaxTile) and a^(2^b).
+    std::vector<uint64_t> lin((size_t)kNumRoots * kPowLinRow), p2((size_t)kNumRoots * 64);
+    for (int r = 0; r < kNumRoots; r++) {
+        uint64_t x = 1;
+        for (int i = 0; i < kPowLinRow; i++) {
+            lin[(size_t)r * kPowLinRow + i] = x;
+            x = mulmod(x, kRoots[r], kQ);
+        }
+        uint64_t y = kRoots[r];
+        for (int b = 0; b < 64; b++) {
+            p2[(size_t)r * 64 + b] = y;
+            y = mulmod(y, y, kQ);
+        }
+    }
+    if ((e = cudaMemcpy(c->d_pow_lin, lin.data(), lin.size() * 8, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(c->d_pow2k, p2.data(), p2.size() * 8, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return cleanup(cuda_fail(e, "power tables"));
+    for (auto &s : c->slots) {
+        if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "event create"));
+    }
+    *out = c;
+    return RSAPRNG_OK;
+}
+
+void rsaprng_ctx_destroy(rsaprng_ctx *c)
+{
+    if (!c)
+        return;
+    cudaSetDevice(c->device);
+    for (auto &s : c->slots) {
+        if (s.used)
+            cudaEventSynchronize(s.done);
+        free_devplan(s.plan);
+        if (s.done)
+            cudaEventDestroy(s.done);
+    }
+    if (c->d_params)
+        cudaFree(c->d_params);
+    if (c->d_m)
+        cudaFree(c->d_m);
+    if (c->d_s)
+        cudaFree(c->d_s);
+    if (c->d_pow_lin)
+        cudaFree(c->d_pow_lin);
+    if (c->d_pow2k)
+        cudaFree(c->d_pow2k);
+    if (c->d_out_scratch)
+        cudaFree(c->d_out_scratch);
+    delete c;
+}
+
+int rsaprng_ctx_configure(rsaprng_ctx *c, const rsaprng_config *cfg)
+{
+    if (!c || !cfg)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    rsaprng_config conf = merged(c->cfg, cfg);
+    int rc = check_config(conf);
+    if (rc)
+        return rc;
+    c->cfg = conf;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_ctx_get_config(const rsaprng_ctx *c, rsaprng_config *out)
+{
+    if (!c || !out)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    *out = c->cfg;
+    return RSAPRNG_OK;
+}
+
+uint64_t rsaprng_instance_count(const rsaprng_ctx *c) { return c ? c->count : 0; }
+
+uint64_t rsaprng_launch_count(const rsaprng_ctx *c) { return c ? c->launches : 0; }
+
+// Appends validated instances [count .. count+k) and writes them to the device.
+static int append_instances(rsaprng_ctx *c, const std::vector<InstParams> &ps,
+                            const std::vector<uint64_t> &m0, const std::vector<uint64_t> &s0,
+                            rsaprng_id *out_first)
+{
+    const uint64_t k = ps.size();
+    if (c->count + k > c->capacity)
+        return fail(RSAPRNG_ERR_CAPACITY, "instance table full (%llu of %llu)",
+                    (unsigned long long)c->count, (unsigned long long)c->capacity);
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if ((e = cudaMemcpy(c->d_params + c->count, ps.data(), k * sizeof(InstParams),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_m + c->count, m0.data(), k * 8, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(c->d_s + c->count, s0.data(), k * 8, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return cuda_fail(e, "instance upload");
+    c->h_params.insert(c->h_params.end(), ps.begin(), ps.end());
+    if (out_first)
+        *out_first = (rsaprng_id)c->count;
+    c->count += k;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_instance_create_ex(rsaprng_ctx *c, uint64_t p, uint64_t q, uint64_t e, uint64_t a,
+                               uint64_t m0, uint64_t s0, rsaprng_id *out)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null ctx");
+    int rc = validate_pqe(p, q, e, c->cfg.require_safe != 0);
+    if (rc)
+        return fail(rc, "instance (p=%llu, q=%llu, e=%llu): %s", (unsigned long long)p,
+                    (unsigned long long)q, (unsigned long long)e, rsaprng_strerror(rc));
+    if (root_index(a) < 0)
+        return fail(RSAPRNG_ERR_ROOT, "a=%llu is not an allowed root", (unsigned long long)a);
+    if (m0 >= p * q || s0 == 0 || s0 >= kQ)
+        return fail(RSAPRNG_ERR_STATE, "start state out of range");
+    std::vector<InstParams> ps(1);
+    make_params(p, q, e, a, ps[0]);
+    return append_instances(c, ps, {m0}, {s0}, out);
+}
+
+int rsaprng_instance_create(rsaprng_ctx *c, uint64_t p, uint64_t q, uint64_t e, uint64_t seed,
+                            rsaprng_id *out)
+{
+    if (p == 0 || q == 0)
+        return fail(RSAPRNG_ERR_RANGE, "p, q must be nonzero");
+    return rsaprng_instance_create_ex(c, p, q, e, RSAPRNG_DEFAULT_ROOT, seed % (p * q), 1, out);
+}
+
+int rsaprng_instances_create_bulk(rsaprng_ctx *c, uint64_t count, const uint64_t *p,
+                                  const uint64_t *q, const uint64_t *e, const uint64_t *seed,
+                                  rsaprng_id *out_first)
+{
+    if (!c || (count && (!p || !q || !e || !seed)))
+        return fail(RSAPRNG_ERR_ARG, "null argument");
+    std::vector<InstParams> ps(count);
+    std::vector<uint64_t> m0(count), s0(count, 1);
+    std::vector<int> err(count, 0);
+    const bool safe = c->cfg.require_safe != 0;
+    parallel_for(count, [&](uint64_t i) {
+        err[i] = validate_pqe(p[i], q[i], e[i], safe);
+        if (!err[i]) {
+            make_params(p[i], q[i], e[i], RSAPRNG_DEFAULT_ROOT, ps[i]);
+            m0[i] = seed[i] % (p[i] * q[i]);
+        }
+    });
+    for (uint64_t i = 0; i < count; i++)
+        if (err[i])
+            return fail(err[i], "entry %llu: %s", (unsigned long long)i, rsaprng_strerror(err[i]));
+    return append_instances(c, ps, m0, s0, out_first);
+}
+
+int rsaprng_instances_create_seeded(rsaprng_ctx *c, uint64_t count, const uint64_t *seeds,
+                                    int e_rule, uint64_t e_lo, uint64_t e_hi,
+                                    rsaprng_id *out_first)
+{
+    if (!c || (count && !seeds))
+        return fail(RSAPRNG_ERR_ARG, "null argument");
+    std::vector<InstParams> ps(count);
+    std::vector<uint64_t> m0(count), s0(count, 1);
+    std::vector<int> err(count, 0);
+    parallel_for(count, [&](uint64_t i) {
+        uint64_t p, q, e, ms;
+        err[i] = rsaprng::params_from_seed(seeds[i], e_rule, e_lo, e_hi, p, q, e, ms);
+        if (!err[i]) {
+            make_params(p, q, e, RSAPRNG_DEFAULT_ROOT, ps[i]);
+            m0[i] = ms % (p * q);
+        }
+    });
+    for (uint64_t i = 0; i < count; i++)
+        if (err[i])
+            return fail(err[i], "seed %llu: %s", (unsigned long long)i, rsaprng_strerror(err[i]));
+    return append_instances(c, ps, m0, s0, out_first);
+}
+
+int rsaprng_get_state(rsaprng_ctx *c, rsaprng_id id, uint64_t *m, uint64_t *s)
+{
+    if (!c || !m || !s)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if ((e = cudaMemcpy(m, c->d_m + id, 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(s, c->d_s + id, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "get_state");
+    return RSAPRNG_OK;
+}
+
+int rsaprng_set_state(rsaprng_ctx *c, rsaprng_id id, uint64_t m, uint64_t s)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    if (m >= c->h_params[id].n || s == 0 || s >= kQ)
+        return fail(RSAPRNG_ERR_STATE, "state out of range");
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if ((e = cudaMemcpy(c->d_m + id, &m, 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_s + id, &s, 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "set_state");
+    return RSAPRNG_OK;
+}
+
+int rsaprng_get_params(rsaprng_ctx *c, rsaprng_id id, uint64_t *p, uint64_t *q, uint64_t *e,
+                       uint64_t *a)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    const InstParams &P = c->h_params[id];
+    if (p)
+        *p = P.p;
+    if (q)
+        *q = P.q;
+    if (e)
+        *e = P.e;
+    if (a)
+        *a = P.a;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_split(rsaprng_ctx *c, rsaprng_id parent, uint32_t Mv, rsaprng_id *out_children)
+{
+    if (!c || !out_children || Mv == 0)
+        return fail(RSAPRNG_ERR_ARG, "split: bad arguments");
+    uint64_t m, s;
+    int rc = rsaprng_get_state(c, parent, &m, &s);
+    if (rc)
+        return rc;
+    const InstParams P = c->h_params[parent];
+    const uint64_t stride = (kQ - 1) / Mv;
+    const uint64_t a_stride = powQ(P.a, stride);
+    std::vector<InstParams> ps(Mv, P);
+    std::vector<uint64_t> m0(Mv, m), s0(Mv);
+    uint64_t x = s;
+    for (uint32_t g = 0; g < Mv; g++) {
+        s0[g] = x;  // s a^(g stride) mod Q
+        x = mulmod(x, a_stride, kQ);
+    }
+    rsaprng_id first;
+    rc = append_instances(c, ps, m0, s0, &first);
+    if (rc)
+        return rc;
+    for (uint32_t g = 0; g < Mv; g++)
+        out_children[g] = first + g;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
+                           const uint64_t *counts, const uint64_t *out_offsets, double *d_r,
+                           uint64_t *d_c, void *stream)
+{
+    if (!c || (nreq && (!ids || !counts || !out_offsets)))
+        return fail(RSAPRNG_ERR_ARG, "generate_batch: null argument");
+    if (!d_r && !d_c)
+        return fail(RSAPRNG_ERR_ARG, "generate_batch: no output buffer");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    HostPlan hp;
+    int rc = build_plan(c, nreq, ids, counts, out_offsets, c->cfg.chunk, hp);
+    if (rc)
+        return rc;
+    if (hp.items.empty())
+        return RSAPRNG_OK;
+    ScratchSlot *slot;
+    if ((rc = scratch_slot(c, &slot)) != RSAPRNG_OK)
+        return rc;
+    if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
+        return rc;
+    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr);
+    cudaEventRecord(slot->done, st);
+    slot->used = true;
+    return rc;
+}
+
+// Splits one instance's N outputs into chunks sized so that every SM gets
+// work, then generates through the batch path.
+static int generate_one(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
+                        void *stream)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null ctx");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    if (N == 0)
+        return RSAPRNG_OK;
+    const uint64_t tile = (uint64_t)c->cfg.threads_per_block * c->cfg.numbers_per_thread;
+    const uint64_t target = (uint64_t)c->sms * 8;
+    uint64_t chunk = (N + target - 1) / target;
+    chunk = std::max<uint64_t>(tile, (chunk + tile - 1) / tile * tile);
+    chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(c->cfg.chunk, tile));
+    rsaprng_config saved = c->cfg;
+    c->cfg.chunk = chunk;
+    const uint64_t zero = 0;
+    int rc = rsaprng_generate_batch(c, 1, &id, &N, &zero, d_r, d_c, stream);
+    c->cfg = saved;
+    return rc;
+}
+
+int rsaprng_generate_u64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c, void *stream)
+{
+    if (!d_c)
+        return fail(RSAPRNG_ERR_ARG, "null output");
+    return generate_one(c, id, N, d_c, nullptr, stream);
+}
+
+int rsaprng_generate_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, double *d_r, void *stream)
+{
+    if (!d_r)
+        return fail(RSAPRNG_ERR_ARG, "null output");
+    return generate_one(c, id, N, nullptr, d_r, stream);
+}
+
+int rsaprng_generate_both(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
+                          void *stream)
+{
+    if (!d_c || !d_r)
+        return fail(RSAPRNG_ERR_ARG, "null output");
+    return generate_one(c, id, N, d_c, d_r, stream);
+}
+
+int rsaprng_unit_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, const uint64_t *d_c,
+                     double *d_r, int divide, void *stream)
+{
+    if (!c || (N && (!d_c || !d_r)))
+        return fail(RSAPRNG_ERR_ARG, "unit_f64: null argument");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    if (divide == RSAPRNG_DIVIDE_AUTO)
+        divide = c->cfg.divide;
+    cudaSetDevice(c->device);
+    cudaError_t e = launch_unit(ctx_tables(c), id, N, d_c, d_r,
+                                divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64 : DIVIDE_INT,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "unit launch");
+    c->launches += N ? 1 : 0;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_microbench(rsaprng_ctx *c, int kind, uint64_t bytes, double *result)
+{
+    if (!c || !result)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    cudaSetDevice(c->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    if (kind == 0) {
+        e = microbench_imad(result, st);
+    } else if (kind == 1) {
+        e = microbench_ddiv(result, st);
+    } else if (kind == 2) {
+        void *buf = nullptr;
+        if (bytes < (1 << 20))
+            bytes = 1 << 20;
+        e = cudaMalloc(&buf, bytes);
+        if (e == cudaSuccess) {
+            e = microbench_write(buf, bytes, result, st);
+            cudaFree(buf);
+        }
+    } else {
+        cudaStreamDestroy(st);
+        return fail(RSAPRNG_ERR_ARG, "unknown microbenchmark %d", kind);
+    }
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "microbenchmark");
+    return RSAPRNG_OK;
+}
+
+}  // extern "C"

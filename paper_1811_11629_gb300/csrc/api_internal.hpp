@@ -1,0 +1,81 @@
+// Internal state of the library's host runtime.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rsaprng.h"
+#include "host_params.hpp"
+#include "kernels.cuh"
+
+namespace rsaprng {
+
+// Work lists of one launch sequence, built on the host.
+struct HostPlan {
+    std::vector<WorkItem> items;
+    std::vector<PrepChunk> chunks;
+    std::vector<PrepGroup> groups;
+    uint64_t numbers = 0;
+};
+
+// The same lists in device memory (one allocation) plus the skip-sum scratch.
+struct DevPlan {
+    void *d_buf = nullptr;
+    size_t cap_buf = 0;
+    void *h_buf = nullptr;  // pinned staging
+    size_t cap_host = 0;
+    void *d_sums = nullptr;
+    size_t cap_sums = 0;
+    WorkItem *items = nullptr;
+    PrepChunk *chunks = nullptr;
+    PrepGroup *groups = nullptr;
+    uint32_t *ticket = nullptr;
+    uint64_t *chunk_sum = nullptr;
+    uint64_t *chunk_s = nullptr;
+    uint32_t nitems = 0, nchunks = 0, ngroups = 0;
+    uint64_t numbers = 0;
+};
+
+constexpr int kScratchSlots = 4;
+struct ScratchSlot {
+    DevPlan plan;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+}  // namespace rsaprng
+
+struct rsaprng_ctx {
+    int device = 0;
+    int sms = 0;
+    uint64_t capacity = 0, count = 0;
+    rsaprng::InstParams *d_params = nullptr;
+    uint64_t *d_m = nullptr, *d_s = nullptr;
+    uint64_t *d_pow_lin = nullptr, *d_pow2k = nullptr;
+    std::vector<rsaprng::InstParams> h_params;  // host mirror of the fixed parameters
+    rsaprng_config cfg{};
+    rsaprng::ScratchSlot slots[rsaprng::kScratchSlots];
+    int next_slot = 0;
+    uint64_t launches = 0;
+    void *d_out_scratch = nullptr;  // device staging for host-buffer generation
+    size_t cap_out_scratch = 0;
+};
+
+namespace rsaprng {
+
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+DeviceTables ctx_tables(rsaprng_ctx *c);
+GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
+                     bool want_c);
+int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
+               const uint64_t *offsets, uint64_t chunk, HostPlan &hp);
+int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
+int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
+                uint64_t *d_c, cudaStream_t stream, uint64_t *launches);
+void free_devplan(DevPlan &dp);
+int scratch_slot(rsaprng_ctx *c, ScratchSlot **out);
+
+}  // namespace rsaprng

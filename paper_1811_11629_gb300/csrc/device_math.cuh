@@ -1,0 +1,243 @@
+// Device arithmetic of the generator (arXiv:1811.11629 Sec. III-V), all exact.
+//
+//  - skip update a s mod Q (Eq. congruentialgenerator1) with Q = 2^63 - 25,
+//    reduced by folding: 2^63 = 25 (mod Q), so hi 2^63 + lo = 25 hi + lo;
+//  - message update (m + s) mod n with n in [2^62, 2^64) (Sec. IV);
+//  - c = m^e mod n (Eq. encrypt2) either by CRT + Garner on two 32-bit
+//    Montgomery exponentiations (Eq. CRTimplementation), or by one 64-bit
+//    Montgomery exponentiation; both are exact, so both give the same c;
+//  - r = RN(RN(c) / RN(n)) with the 1.0 guard (Eq. CodeFloatingPointStep),
+//    either with IEEE double operations or with integers only.
+#pragma once
+#include <cstdint>
+
+#include "host_params.hpp"
+
+namespace rsaprng {
+namespace dev {
+
+constexpr u64 Q = 0x7FFFFFFFFFFFFFE7ULL;
+constexpr u64 LOW63 = 0x7FFFFFFFFFFFFFFFULL;
+
+// a s mod Q for a < 2^32 and s < Q: the product is below 2^95.
+__device__ __forceinline__ u64 mulmodQ_small(u64 s, u32 a)
+{
+    const u64 p0 = (u64)(u32)s * a;          // s_lo * a
+    const u64 p1 = (u64)(u32)(s >> 32) * a;  // s_hi * a, below 2^63
+    const u64 lo = p0 + (p1 << 32);
+    const u64 hi = (p1 >> 32) + (lo < p0 ? 1 : 0);
+    // x = hi 2^64 + lo = H 2^63 + L63 with H = 2 hi + lo_63 < 2^33
+    const u64 H = (hi << 1) | (lo >> 63);
+    u64 y = H * 25 + (lo & LOW63);  // < 2^63 + 2^38 < 2Q
+    return y >= Q ? y - Q : y;
+}
+
+// x y mod Q for x, y < Q (general 63-bit multiplier).
+__device__ __forceinline__ u64 mulmodQ(u64 x, u64 y)
+{
+    const u64 lo = x * y;
+    const u64 hi = __umul64hi(x, y);           // < 2^62
+    const u64 H = (hi << 1) | (lo >> 63);      // < 2^63
+    // 25 H + L63 in 128 bits
+    const u64 t_lo = H * 25;
+    const u64 t_hi = __umul64hi(H, 25ULL);
+    const u64 y_lo = t_lo + (lo & LOW63);
+    const u64 y_hi = t_hi + (y_lo < t_lo ? 1 : 0);  // y = y_hi 2^64 + y_lo < 26 2^63
+    const u64 H2 = (y_hi << 1) | (y_lo >> 63);       // <= 25
+    const u64 z = H2 * 25 + (y_lo & LOW63);           // < 2^63 + 2^10
+    return z >= Q ? z - Q : z;
+}
+
+// (a + b) mod n for a, b < n < 2^64 (the sum may carry out of 64 bits).
+__device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 n)
+{
+    const u64 s = a + b;
+    return (s < a || s >= n) ? s - n : s;
+}
+
+// s mod n for a skip s < Q: since n >= 2^62, Q < 2n.
+__device__ __forceinline__ u64 skip_mod_n(u64 s, u64 n) { return s >= n ? s - n : s; }
+
+// Montgomery product a b 2^-32 mod p for a, b < p < 2^32, p odd, pinv =
+// p^-1 mod 2^32. With mq = T_lo pinv, mq p = T (mod 2^32) exactly, so
+// T - mq p = (T_hi - hi(mq p)) 2^32 and the difference lies in (-p, p).
+__device__ __forceinline__ u32 redc32(u64 T, u32 p, u32 pinv)
+{
+    const u32 mq = (u32)T * pinv;
+    const u32 u = __umulhi(mq, p);
+    const u32 th = (u32)(T >> 32);
+    const u32 r = th - u;
+    return th < u ? r + p : r;
+}
+__device__ __forceinline__ u32 mont32(u32 a, u32 b, u32 p, u32 pinv)
+{
+    return redc32((u64)a * b, p, pinv);
+}
+
+// Montgomery product a b 2^-64 mod n for a, b < n, n odd, ninv = n^-1 mod 2^64.
+__device__ __forceinline__ u64 mont64(u64 a, u64 b, u64 n, u64 ninv)
+{
+    const u64 lo = a * b;
+    const u64 hi = __umul64hi(a, b);
+    const u64 mq = lo * ninv;
+    const u64 u = __umul64hi(mq, n);
+    const u64 r = hi - u;
+    return hi < u ? r + n : r;
+}
+
+// c_j = m_j^e mod n for L messages by CRT (Eq. CRTimplementation): the
+// residues enter as REDC(m) = m 2^-32 mod p (and mod q), left-to-right
+// square-and-multiply runs on them with Montgomery products (Sec. I), the
+// constants kp = 2^(64e) mod p, kq remove the Montgomery factors, and Garner's
+// formula recombines: c = ((c_p - c_q) q^-1 mod p) q + c_q.
+template <int L>
+__device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
+{
+    const u32 p = P.p, q = P.q, pinv = P.pinv, qinv = P.qinv, e = P.e;
+    u32 yp[L], yq[L], zp[L], zq[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        yp[j] = redc32(m[j], p, pinv);
+        yq[j] = redc32(m[j], q, qinv);
+        zp[j] = yp[j];
+        zq[j] = yq[j];
+    }
+    const int top = 31 - __clz(e);
+    for (int bit = top - 1; bit >= 0; bit--) {
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            zp[j] = mont32(zp[j], zp[j], p, pinv);
+            zq[j] = mont32(zq[j], zq[j], q, qinv);
+        }
+        if ((e >> bit) & 1) {
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                zp[j] = mont32(zp[j], yp[j], p, pinv);
+                zq[j] = mont32(zq[j], yq[j], q, qinv);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const u32 cp = mont32(zp[j], P.kp, p, pinv);
+        const u32 cq = mont32(zq[j], P.kq, q, qinv);
+        const u32 cqp = cq >= p ? cq - p : cq;  // q < 2p
+        u32 diff = cp - cqp;
+        if (cp < cqp)
+            diff += p;
+        const u32 h = mont32(diff, P.garner, p, pinv);  // (c_p - c_q) q^-1 mod p
+        c[j] = (u64)h * q + cq;
+    }
+}
+
+// c_j = m_j^e mod n with 64-bit Montgomery products on the plain message:
+// the chain ends at m^e 2^(64(1-e)); the product with kn = 2^(64e) mod n
+// gives m^e mod n.
+template <int L>
+__device__ __forceinline__ void encrypt_mont64(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
+{
+    const u64 n = P.n, ninv = P.ninv;
+    const u32 e = P.e;
+    u64 z[L];
+#pragma unroll
+    for (int j = 0; j < L; j++)
+        z[j] = m[j];
+    const int top = 31 - __clz(e);
+    for (int bit = top - 1; bit >= 0; bit--) {
+#pragma unroll
+        for (int j = 0; j < L; j++)
+            z[j] = mont64(z[j], z[j], n, ninv);
+        if ((e >> bit) & 1) {
+#pragma unroll
+            for (int j = 0; j < L; j++)
+                z[j] = mont64(z[j], m[j], n, ninv);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < L; j++)
+        c[j] = mont64(z[j], P.kn, n, ninv);
+}
+
+constexpr u64 ONE_MINUS_ULP_BITS = 0x3FEFFFFFFFFFFFFFULL;  // 1 - 2^-53
+
+// r = RN(RN(c)/RN(n)) with IEEE double conversion and division.
+__device__ __forceinline__ double unit_fp64(u64 c, u64 n)
+{
+    const double r = __ddiv_rn(__ull2double_rn(c), __ull2double_rn(n));
+    return r >= 1.0 ? __longlong_as_double((long long)ONE_MINUS_ULP_BITS) : r;
+}
+
+// The same value from integers only. RN(c) = Mc 2^Ec is rounded to 53 bits
+// with ties to even; RN(n) = Mn 2^En is a per-instance constant. The
+// significand quotient X / Mn with X = Mc 2^52 (Mc >= Mn) or Mc 2^53
+// (Mc < Mn) lies in [2^52, 2^53); it is computed exactly, with remainder, by
+// division by the invariant normalised divisor d = Mn 2^11 using the
+// precomputed reciprocal v (Moller & Granlund, "Improved division by
+// invariant integers", IEEE TC 2011, 2/1 division), then rounded to nearest
+// even by comparing the remainder with d/2, and packed into a double.
+__device__ __forceinline__ double unit_int(u64 c, const InstParams &P)
+{
+    if (c == 0)
+        return 0.0;
+    const int b = 64 - __clzll(c);
+    u64 mc;
+    int ec;
+    if (b <= 53) {
+        mc = c << (53 - b);
+        ec = b - 53;
+    } else {
+        const int sh = b - 53;
+        mc = c >> sh;
+        const u64 rem = c & ((1ULL << sh) - 1);
+        const u64 half = 1ULL << (sh - 1);
+        if (rem > half || (rem == half && (mc & 1)))
+            mc++;
+        ec = sh;
+        if (mc >> 53) {
+            mc >>= 1;
+            ec++;
+        }
+    }
+    const u64 d = P.dnorm, v = P.dv;
+    const u64 mn = d >> 11;
+    u64 u1, u0;
+    int E;
+    if (mc >= mn) {
+        u1 = mc >> 1;
+        u0 = mc << 63;
+        E = ec - P.en;
+    } else {
+        u1 = mc;
+        u0 = 0;
+        E = ec - P.en - 1;
+    }
+    // (q1, q0) = v u1 + (u1, u0)
+    u64 q0 = v * u1;
+    u64 q1 = __umul64hi(v, u1);
+    q0 += u0;
+    q1 += u1 + (q0 < u0 ? 1 : 0);
+    q1 += 1;
+    u64 r = u0 - q1 * d;
+    if (r > q0) {
+        q1 -= 1;
+        r += d;
+    }
+    if (r >= d) {
+        q1 += 1;
+        r -= d;
+    }
+    const u64 halfd = d >> 1;
+    if (r > halfd || (r == halfd && (q1 & 1)))
+        q1++;
+    if (q1 >> 53) {
+        q1 >>= 1;
+        E++;
+    }
+    u64 bits = ((u64)(E + 1023) << 52) | (q1 & ((1ULL << 52) - 1));
+    if (bits > ONE_MINUS_ULP_BITS)
+        bits = ONE_MINUS_ULP_BITS;
+    return __longlong_as_double((long long)bits);
+}
+
+}  // namespace dev
+}  // namespace rsaprng

@@ -1,0 +1,536 @@
+// Generation kernels for the RSA-exponentiation generator (arXiv:1811.11629).
+//
+// Tile engine. A block of T threads walks one stream in tiles of S = T L
+// outputs; thread t owns the L consecutive outputs tL+1 .. tL+L of a tile:
+//   1. skips: its first skip is s_tile a^(tL) (power table), then L steps of
+//      s <- a s mod Q with the 32-bit multiplier (Eq. congruentialgenerator1);
+//   2. messages: the skips (mod n) are summed per thread, a block-wide
+//      exclusive scan mod n gives each thread the message before its run,
+//      and a running carry links the tiles (Sec. IV, m_k = m_{k-1} + s_k);
+//   3. encryption of the L messages as independent chains (Eq. encrypt2);
+//   4. r = c / n (Eq. CodeFloatingPointStep) and the 1.0 guard;
+//   5. outputs are staged in shared memory and written with coalesced stores.
+// Long streams are cut into chunks; a skip-sum pass over the chunks and a
+// scan per instance give every chunk its start state, so no block ever waits
+// for another (no inter-block spin).
+#include <cstdio>
+
+#include "device_math.cuh"
+#include "kernels.cuh"
+
+namespace rsaprng {
+
+using dev::addmod;
+using dev::mulmodQ;
+using dev::mulmodQ_small;
+using dev::skip_mod_n;
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Padded shared-memory index: one 8-byte slot of padding every 16 elements
+// spreads the stride-L writes of a warp over the banks.
+__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
+
+// Block-wide exclusive scan of v (mod n). Returns the exclusive prefix and
+// the block total. sh must hold 32 entries. Contains two __syncthreads().
+__device__ __forceinline__ u64 block_exscan_mod(u64 v, u64 n, u64 *sh, u64 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    u64 incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const u64 o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d)
+            incl = addmod(incl, o, n);
+    }
+    if (lane == 31)
+        sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        u64 w = lane < nwarps ? sh[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const u64 o = __shfl_up_sync(FULL, w, d);
+            if (lane >= d)
+                w = addmod(w, o, n);
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    total = sh[nwarps - 1];
+    const u64 wpre = warp > 0 ? sh[warp - 1] : 0;
+    u64 ex = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0)
+        ex = 0;
+    return addmod(wpre, ex, n);
+}
+
+__device__ __forceinline__ u64 block_reduce_mod(u64 v, u64 n, u64 *sh)
+{
+    u64 total;
+    (void)block_exscan_mod(v, n, sh, total);
+    return total;
+}
+
+template <int L, int MODEXP>
+__device__ __forceinline__ void encrypt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
+{
+    if constexpr (MODEXP == MODEXP_CRT32)
+        dev::encrypt_crt<L>(m, c, P);
+    else
+        dev::encrypt_mont64<L>(m, c, P);
+}
+
+template <int DIV>
+__device__ __forceinline__ double to_unit(u64 c, const InstParams &P)
+{
+    if constexpr (DIV == DIVIDE_INT)
+        return dev::unit_int(c, P);
+    else
+        return dev::unit_fp64(c, P.n);
+}
+
+template <int L, int MODEXP, int DIV>
+__global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
+                                                  uint32_t nitems, uint32_t *ticket,
+                                                  double *__restrict__ out_r,
+                                                  u64 *__restrict__ out_c)
+{
+    extern __shared__ u64 smem[];
+    __shared__ u64 sh_scan[32];
+    __shared__ uint32_t sh_item;
+    const int T = blockDim.x, t = threadIdx.x;
+    const int S = T * L;
+    const int slots = S + (S >> 4);
+    u64 *st_r = smem;
+    u64 *st_c = smem + (out_r ? slots : 0);
+
+    uint32_t it = blockIdx.x;
+    if (ticket) {
+        if (t == 0)
+            sh_item = atomicAdd(ticket, 1u);
+        __syncthreads();
+        it = sh_item;
+    }
+    while (it < nitems) {
+        const WorkItem W = items[it];
+        const InstParams P = tab.params[W.inst];
+        const u64 n = P.n;
+        const u32 a = P.a;
+        const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
+        u64 m, s;
+        if (W.flags & WI_FROM_STATE) {
+            m = tab.state_m[W.inst];
+            s = tab.state_s[W.inst];
+        } else {
+            m = W.m0;
+            s = W.s0;
+        }
+        // Skip at the start of this thread's run in the first tile.
+        u64 s_thr = mulmodQ(s, plin[t * L]);
+        const u64 aS = plin[S];
+        const u64 count = W.count;
+        for (u64 base = 0; base < count; base += S) {
+            const u64 left = count - base;
+            const int tile_n = left < (u64)S ? (int)left : S;
+            const int my0 = t * L;
+            const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0);
+            u64 sk[L];
+            u64 x = s_thr, sum = 0, s_last = 0;
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                x = mulmodQ_small(x, a);
+                sk[j] = skip_mod_n(x, n);
+                if (j < nvalid) {
+                    sum = addmod(sum, sk[j], n);
+                    s_last = x;
+                }
+            }
+            u64 total;
+            const u64 pre = block_exscan_mod(sum, n, sh_scan, total);
+            u64 msg[L];
+            u64 mm = addmod(m, pre, n);
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                mm = addmod(mm, sk[j], n);
+                msg[j] = mm;
+            }
+            if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
+                tab.state_s[W.inst] = s_last;  // this thread owns the stream's last output
+            u64 c[L];
+            encrypt<L, MODEXP>(msg, c, P);
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                const int i = sidx(my0 + j);
+                if (out_r)
+                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P));
+                if (out_c)
+                    st_c[i] = c[j];
+            }
+            __syncthreads();
+            const u64 o = W.out_off + base;
+            if (out_r) {
+                for (int i = t; i < tile_n; i += T)
+                    out_r[o + i] = __longlong_as_double((long long)st_r[sidx(i)]);
+            }
+            if (out_c) {
+                for (int i = t; i < tile_n; i += T)
+                    out_c[o + i] = st_c[sidx(i)];
+            }
+            __syncthreads();
+            m = addmod(m, total, n);
+            s_thr = mulmodQ(s_thr, aS);
+        }
+        if ((W.flags & WI_WRITEBACK) && t == 0) {
+            tab.state_m[W.inst] = m;
+            if (count == 0)
+                tab.state_s[W.inst] = s;
+        }
+        if (ticket) {
+            __syncthreads();
+            if (t == 0)
+                sh_item = atomicAdd(ticket, 1u);
+            __syncthreads();
+            it = sh_item;
+        } else {
+            it += gridDim.x;
+        }
+    }
+}
+
+// Skip sums of chunks: for chunk k with start offset o and length len,
+// chunk_s[k] = s a^o mod Q (the skip before its first output) and
+// chunk_sum[k] = sum_{x=1..len} (s a^(o+x) mod Q) mod n, where s is the
+// instance's current skip. One block per chunk, 256 threads x 8 skips a tile.
+constexpr int kPrepT = 256;
+constexpr int kPrepL = 8;
+__global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
+                                                     const PrepChunk *__restrict__ chunks,
+                                                     uint32_t nchunks, u64 *__restrict__ chunk_sum,
+                                                     u64 *__restrict__ chunk_s)
+{
+    __shared__ u64 sh_scan[32];
+    __shared__ u64 sh_s0;
+    const int t = threadIdx.x;
+    for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
+        const PrepChunk C = chunks[k];
+        const InstParams P = tab.params[C.inst];
+        const u64 n = P.n;
+        const u32 a = P.a;
+        const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
+        const u64 *p2k = tab.pow2k + (size_t)P.root * 64;
+        if (t == 0) {
+            u64 s = tab.state_s[C.inst];
+            for (int b = 0; b < 64; b++)
+                if ((C.offset >> b) & 1)
+                    s = mulmodQ(s, p2k[b]);
+            sh_s0 = s;
+            chunk_s[k] = s;
+        }
+        __syncthreads();
+        const u64 s0 = sh_s0;
+        constexpr int S = kPrepT * kPrepL;
+        u64 s_thr = mulmodQ(s0, plin[t * kPrepL]);
+        const u64 aS = plin[S];
+        u64 acc = 0;
+        for (u64 base = 0; base < C.len; base += S) {
+            const u64 left = C.len - base;
+            const int my0 = t * kPrepL;
+            const int tile_n = left < (u64)S ? (int)left : S;
+            const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > kPrepL ? kPrepL : tile_n - my0);
+            u64 x = s_thr;
+#pragma unroll
+            for (int j = 0; j < kPrepL; j++) {
+                x = mulmodQ_small(x, a);
+                if (j < nvalid)
+                    acc = addmod(acc, skip_mod_n(x, n), n);
+            }
+            s_thr = mulmodQ(s_thr, aS);
+        }
+        const u64 tot = block_reduce_mod(acc, n, sh_scan);
+        if (t == 0)
+            chunk_sum[k] = tot;
+        __syncthreads();
+    }
+}
+
+// Start states of the chunks of each instance: m before chunk j is the
+// instance's m plus the skip sums of chunks 0..j-1 (mod n).
+__global__ void k_prep_scan(DeviceTables tab, const PrepGroup *__restrict__ groups, uint32_t ngroups,
+                            const PrepChunk *__restrict__ chunks, const u64 *__restrict__ chunk_sum,
+                            const u64 *__restrict__ chunk_s, WorkItem *__restrict__ items)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups)
+        return;
+    const PrepGroup G = groups[g];
+    const u64 n = tab.params[G.inst].n;
+    u64 m = tab.state_m[G.inst];
+    for (uint32_t j = 0; j < G.count; j++) {
+        const uint32_t k = G.first + j;
+        WorkItem &w = items[chunks[k].item];
+        w.m0 = m;
+        w.s0 = chunk_s[k];
+        m = addmod(m, chunk_sum[k], n);
+    }
+}
+
+template <int L, int MODEXP, int DIV>
+cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                         uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
+                         cudaStream_t stream)
+{
+    const size_t smem = gen_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
+    auto kern = k_generate<L, MODEXP, DIV>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    kern<<<g.grid, g.threads, smem, stream>>>(t, items, nitems, g.persistent ? ticket : nullptr,
+                                              out_r, out_c);
+    return cudaGetLastError();
+}
+
+template <int L, int MODEXP, int DIV>
+const void *gen_kernel_ptr()
+{
+    return (const void *)k_generate<L, MODEXP, DIV>;
+}
+
+const void *select_kernel(int L, int modexp, int divide)
+{
+#define RSAPRNG_SEL(LL, MM, DD)                                   \
+    if (L == LL && modexp == MM && divide == DD)                  \
+        return gen_kernel_ptr<LL, MM, DD>();
+    RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_FP64)
+#undef RSAPRNG_SEL
+    return nullptr;
+}
+
+// The output step alone: r[i] = RN(RN(c[i]) / RN(n)) with the 1.0 guard.
+template <int DIV>
+__global__ void k_unit(const InstParams *__restrict__ params, uint32_t id,
+                       const u64 *__restrict__ c, double *__restrict__ r, u64 N)
+{
+    const InstParams P = params[id];
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        r[i] = to_unit<DIV>(c[i], P);
+}
+
+// ---------------------------------------------------------------- microbenchmarks
+
+// 32-bit integer multiply-add throughput: each thread runs 8 independent
+// chains of x <- x * k + c (IMAD) so the pipe, not latency, is the limit.
+__global__ void k_mb_imad(uint32_t iters, uint32_t seed, uint32_t *sink)
+{
+    uint32_t x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        x[j] = seed + threadIdx.x * 8 + j;
+    const uint32_t k = 0x9E3779B1u ^ seed;
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            x[j] = x[j] * k + (uint32_t)j;
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        acc ^= x[j];
+    if (acc == 0x12345678u)
+        sink[0] = acc;
+}
+
+__global__ void k_mb_ddiv(uint32_t iters, double seed, double *sink)
+{
+    double x[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        x[j] = seed + threadIdx.x + j;
+    const double d = 1.0000001;
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            x[j] = __ddiv_rn(x[j], d);
+    }
+    double acc = x[0] + x[1] + x[2] + x[3];
+    if (acc == 1.2345)
+        sink[0] = acc;
+}
+
+__global__ void k_mb_write(uint4 *buf, size_t n16)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+        buf[i] = make_uint4((uint32_t)i, 1u, 2u, 3u);
+}
+
+int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <typename F>
+cudaError_t time_it(F &&launch, cudaStream_t stream, float *ms)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    launch();  // warm-up
+    cudaEventRecord(a, stream);
+    launch();
+    cudaEventRecord(b, stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess)
+        return e;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c)
+{
+    const size_t S = (size_t)threads * L;
+    const size_t slots = S + (S >> 4);
+    return slots * 8 * ((want_r ? 1 : 0) + (want_c ? 1 : 0));
+}
+
+cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                            uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
+                            cudaStream_t stream)
+{
+#define RSAPRNG_DISPATCH(LL, MM, DD)                                                      \
+    if (g.L == LL && g.modexp == MM && g.divide == DD)                                    \
+        return launch_gen_t<LL, MM, DD>(g, t, items, nitems, ticket, out_r, out_c, stream);
+    RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_INT)
+    RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_FP64)
+#undef RSAPRNG_DISPATCH
+    return cudaErrorInvalidValue;
+}
+
+int gen_blocks_per_sm(const GenLaunch &g, size_t smem)
+{
+    const void *k = select_kernel(g.L, g.modexp, g.divide);
+    if (!k)
+        return 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, g.threads, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t launch_prep_sums(const DeviceTables &t, const PrepChunk *chunks, uint32_t nchunks,
+                             uint64_t *chunk_sum, uint64_t *chunk_s, cudaStream_t stream)
+{
+    if (nchunks == 0)
+        return cudaSuccess;
+    const int grid = (int)(nchunks < 65535u ? nchunks : 65535u);
+    k_prep_sums<<<grid, kPrepT, 0, stream>>>(t, chunks, nchunks, chunk_sum, chunk_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_scan(const DeviceTables &t, const PrepGroup *groups, uint32_t ngroups,
+                             const PrepChunk *chunks, const uint64_t *chunk_sum,
+                             const uint64_t *chunk_s, WorkItem *items, cudaStream_t stream)
+{
+    if (ngroups == 0)
+        return cudaSuccess;
+    const int threads = 128;
+    const int grid = (int)((ngroups + threads - 1) / threads);
+    k_prep_scan<<<grid, threads, 0, stream>>>(t, groups, ngroups, chunks, chunk_sum, chunk_s,
+                                              items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const uint64_t *c,
+                        double *r, int divide, cudaStream_t stream)
+{
+    if (N == 0)
+        return cudaSuccess;
+    const int grid = num_sms() * 8;
+    if (divide == DIVIDE_FP64)
+        k_unit<DIVIDE_FP64><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
+    else
+        k_unit<DIVIDE_INT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
+    return cudaGetLastError();
+}
+
+cudaError_t microbench_imad(double *gops, cudaStream_t stream)
+{
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 64);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = num_sms();
+    const int grid = sms * 8, threads = 256;
+    const uint32_t iters = 1 << 16;
+    float ms = 0;
+    e = time_it([&] { k_mb_imad<<<grid, threads, 0, stream>>>(iters, 7u, sink); }, stream, &ms);
+    cudaFree(sink);
+    *gops = (double)grid * threads * iters * 8 / (ms * 1e-3) / 1e9;
+    return e;
+}
+
+cudaError_t microbench_ddiv(double *gdiv, cudaStream_t stream)
+{
+    double *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 64);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = num_sms();
+    const int grid = sms * 8, threads = 256;
+    const uint32_t iters = 1 << 10;
+    float ms = 0;
+    e = time_it([&] { k_mb_ddiv<<<grid, threads, 0, stream>>>(iters, 3.0, sink); }, stream, &ms);
+    cudaFree(sink);
+    *gdiv = (double)grid * threads * iters * 4 / (ms * 1e-3) / 1e9;
+    return e;
+}
+
+cudaError_t microbench_write(void *buf, size_t bytes, double *gbs, cudaStream_t stream)
+{
+    const int sms = num_sms();
+    const size_t n16 = bytes / 16;
+    float ms = 0;
+    cudaError_t e = time_it(
+        [&] { k_mb_write<<<sms * 8, 512, 0, stream>>>((uint4 *)buf, n16); }, stream, &ms);
+    *gbs = (double)n16 * 16 / (ms * 1e-3) / 1e9;
+    return e;
+}
+
+}  // namespace rsaprng

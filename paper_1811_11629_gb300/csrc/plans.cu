@@ -1,0 +1,376 @@
+// Launch plans, CUDA-graph capture, host-buffer generation and the autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "api_internal.hpp"
+
+using namespace rsaprng;
+
+struct rsaprng_plan {
+    rsaprng_ctx *ctx = nullptr;
+    DevPlan dp;
+    rsaprng_config cfg{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+void destroy_graph(rsaprng_plan *p)
+{
+    if (p->exec)
+        cudaGraphExecDestroy(p->exec);
+    if (p->graph)
+        cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
+int plan_create_cfg(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
+                    const uint64_t *counts, const uint64_t *offsets, rsaprng_plan **out)
+{
+    HostPlan hp;
+    int rc = build_plan(c, nreq, ids, counts, offsets, cfg.chunk, hp);
+    if (rc)
+        return rc;
+    rsaprng_plan *p = new (std::nothrow) rsaprng_plan();
+    if (!p)
+        return fail(RSAPRNG_ERR_OOM, "plan alloc");
+    p->ctx = c;
+    p->cfg = cfg;
+    cudaSetDevice(c->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    rc = upload_plan(c, hp, p->dp, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc == RSAPRNG_OK && e != cudaSuccess)
+        rc = cuda_fail(e, "plan upload");
+    if (rc) {
+        free_devplan(p->dp);
+        delete p;
+        return rc;
+    }
+    p->launches = (p->dp.nchunks ? 2 : 0) + (p->dp.nitems ? 1 : 0);
+    *out = p;
+    return RSAPRNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rsaprng_plan_create(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
+                        const uint64_t *counts, const uint64_t *out_offsets, rsaprng_plan **out)
+{
+    if (!c || !out || (nreq && (!ids || !counts || !out_offsets)))
+        return fail(RSAPRNG_ERR_ARG, "plan_create: null argument");
+    return plan_create_cfg(c, c->cfg, nreq, ids, counts, out_offsets, out);
+}
+
+int rsaprng_plan_launch(rsaprng_plan *p, double *d_r, uint64_t *d_c, void *stream)
+{
+    if (!p || (!d_r && !d_c))
+        return fail(RSAPRNG_ERR_ARG, "plan_launch: bad arguments");
+    cudaSetDevice(p->ctx->device);
+    return launch_plan(p->ctx, p->cfg, p->dp, d_r, d_c, (cudaStream_t)stream, nullptr);
+}
+
+int rsaprng_plan_capture(rsaprng_plan *p, double *d_r, uint64_t *d_c, void *stream)
+{
+    if (!p || (!d_r && !d_c) || !stream)
+        return fail(RSAPRNG_ERR_ARG, "plan_capture: needs outputs and a non-default stream");
+    cudaSetDevice(p->ctx->device);
+    destroy_graph(p);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Resolve kernel attributes before capture (occupancy queries are not
+    // stream work).
+    (void)ctx_launch(p->ctx, p->cfg, p->dp.nitems, d_r != nullptr, d_c != nullptr);
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+    const uint64_t before = p->ctx->launches;
+    int rc = launch_plan(p->ctx, p->cfg, p->dp, d_r, d_c, st, nullptr);
+    p->ctx->launches = before;  // recorded, not launched
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (rc)
+        return rc;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "end capture");
+    p->graph = g;
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) {
+        destroy_graph(p);
+        return cuda_fail(e, "graph instantiate");
+    }
+    return RSAPRNG_OK;
+}
+
+int rsaprng_plan_replay(rsaprng_plan *p, void *stream)
+{
+    if (!p || !p->exec)
+        return fail(RSAPRNG_ERR_ARG, "plan_replay: no captured graph");
+    cudaSetDevice(p->ctx->device);
+    cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "graph launch");
+    p->ctx->launches += p->launches;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_plan_info(const rsaprng_plan *p, uint64_t *launches, uint64_t *numbers,
+                      uint64_t *chunks)
+{
+    if (!p)
+        return fail(RSAPRNG_ERR_ARG, "null plan");
+    if (launches)
+        *launches = p->launches;
+    if (numbers)
+        *numbers = p->dp.numbers;
+    if (chunks)
+        *chunks = p->dp.nitems;
+    return RSAPRNG_OK;
+}
+
+void rsaprng_plan_destroy(rsaprng_plan *p)
+{
+    if (!p)
+        return;
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    destroy_graph(p);
+    free_devplan(p->dp);
+    delete p;
+}
+
+// Host-buffer generation: the requests are cut into slices of about equal
+// output size; each slice is generated into one of two device buffers on
+// the caller's stream and copied to the host on a second stream, so the copy
+// of slice k overlaps the generation of slice k+1.
+int rsaprng_generate_batch_host(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
+                                const uint64_t *counts, const uint64_t *out_offsets, double *h_r,
+                                uint64_t *h_c, void *stream)
+{
+    if (!c || (nreq && (!ids || !counts || !out_offsets)) || (!h_r && !h_c))
+        return fail(RSAPRNG_ERR_ARG, "generate_batch_host: bad arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t total = 0;
+    for (uint64_t i = 0; i < nreq; i++)
+        total += counts[i];
+    if (total == 0)
+        return RSAPRNG_OK;
+    const int nslices = (int)std::min<uint64_t>(8, std::max<uint64_t>(1, total >> 22));
+    const uint64_t per = (total + nslices - 1) / nslices;
+    const size_t width = (h_r ? 8 : 0) + (h_c ? 8 : 0);
+    const size_t need = 2 * per * width;
+    if (need > c->cap_out_scratch) {
+        if (c->d_out_scratch) {
+            cudaDeviceSynchronize();
+            cudaFree(c->d_out_scratch);
+        }
+        c->d_out_scratch = nullptr;
+        c->cap_out_scratch = 0;
+        cudaError_t e = cudaMalloc(&c->d_out_scratch, need);
+        if (e != cudaSuccess)
+            return fail(RSAPRNG_ERR_OOM, "host-generation staging (%zu B): %s", need,
+                        cudaGetErrorString(e));
+        c->cap_out_scratch = need;
+    }
+    cudaStream_t cp;
+    cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking);
+    cudaEvent_t gen_done[2], copy_done[2];
+    for (int k = 0; k < 2; k++) {
+        cudaEventCreateWithFlags(&gen_done[k], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&copy_done[k], cudaEventDisableTiming);
+    }
+    struct Part {
+        rsaprng_id id;
+        uint64_t count, dev_off, host_off;
+    };
+    std::vector<Part> parts;
+    std::vector<rsaprng_id> sid;
+    std::vector<uint64_t> scnt, soff;
+    int rc = RSAPRNG_OK;
+    uint64_t req = 0, done_in_req = 0;
+    bool copy_pending[2] = {false, false};
+    for (int k = 0; k < nslices && rc == RSAPRNG_OK; k++) {
+        const int buf = k & 1;
+        parts.clear();
+        uint64_t fill = 0;
+        while (req < nreq && fill < per) {
+            const uint64_t left = counts[req] - done_in_req;
+            const uint64_t take = std::min(left, per - fill);
+            if (take)
+                parts.push_back({ids[req], take, fill, out_offsets[req] + done_in_req});
+            fill += take;
+            done_in_req += take;
+            if (done_in_req == counts[req]) {
+                req++;
+                done_in_req = 0;
+            }
+        }
+        if (parts.empty())
+            break;
+        sid.resize(parts.size());
+        scnt.resize(parts.size());
+        soff.resize(parts.size());
+        for (size_t i = 0; i < parts.size(); i++) {
+            sid[i] = parts[i].id;
+            scnt[i] = parts[i].count;
+            soff[i] = parts[i].dev_off;
+        }
+        char *base = (char *)c->d_out_scratch + (size_t)buf * per * width;
+        double *d_r = h_r ? (double *)base : nullptr;
+        uint64_t *d_c = h_c ? (uint64_t *)(base + (h_r ? per * 8 : 0)) : nullptr;
+        if (copy_pending[buf])
+            cudaStreamWaitEvent(st, copy_done[buf], 0);
+        rc = rsaprng_generate_batch(c, parts.size(), sid.data(), scnt.data(), soff.data(), d_r, d_c,
+                                    stream);
+        if (rc)
+            break;
+        cudaEventRecord(gen_done[buf], st);
+        cudaStreamWaitEvent(cp, gen_done[buf], 0);
+        // One copy per run of parts that is contiguous on the host.
+        for (size_t i = 0; i < parts.size();) {
+            size_t j = i + 1;
+            while (j < parts.size() &&
+                   parts[j].host_off == parts[j - 1].host_off + parts[j - 1].count &&
+                   parts[j].dev_off == parts[j - 1].dev_off + parts[j - 1].count)
+                j++;
+            const uint64_t n = parts[j - 1].dev_off + parts[j - 1].count - parts[i].dev_off;
+            cudaError_t e = cudaSuccess;
+            if (h_r)
+                e = cudaMemcpyAsync(h_r + parts[i].host_off, d_r + parts[i].dev_off, n * 8,
+                                    cudaMemcpyDeviceToHost, cp);
+            if (e == cudaSuccess && h_c)
+                e = cudaMemcpyAsync(h_c + parts[i].host_off, d_c + parts[i].dev_off, n * 8,
+                                    cudaMemcpyDeviceToHost, cp);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "result copy");
+                break;
+            }
+            i = j;
+        }
+        cudaEventRecord(copy_done[buf], cp);
+        copy_pending[buf] = true;
+    }
+    cudaError_t e = cudaStreamSynchronize(cp);
+    if (rc == RSAPRNG_OK && e != cudaSuccess)
+        rc = cuda_fail(e, "result copy");
+    for (int k = 0; k < 2; k++) {
+        cudaEventDestroy(gen_done[k]);
+        cudaEventDestroy(copy_done[k]);
+    }
+    cudaStreamDestroy(cp);
+    return rc;
+}
+
+// Times candidate configurations on the given requests. Instance states are
+// saved first and restored after every trial, so tuning does not advance
+// any stream.
+int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
+                     int reps, rsaprng_config *chosen)
+{
+    if (!c || !nreq || !ids || !counts)
+        return fail(RSAPRNG_ERR_ARG, "autotune: bad arguments");
+    if (reps < 1)
+        reps = 1;
+    cudaSetDevice(c->device);
+    std::vector<uint64_t> offs(nreq);
+    uint64_t total = 0;
+    for (uint64_t i = 0; i < nreq; i++) {
+        offs[i] = total;
+        total += counts[i];
+    }
+    double *d_r = nullptr;
+    uint64_t *save = nullptr;
+    cudaError_t e = cudaMalloc(&d_r, std::max<uint64_t>(total, 1) * 8);
+    if (e != cudaSuccess)
+        return fail(RSAPRNG_ERR_OOM, "autotune output (%llu numbers)", (unsigned long long)total);
+    e = cudaMalloc(&save, c->count * 16);
+    if (e != cudaSuccess) {
+        cudaFree(d_r);
+        return fail(RSAPRNG_ERR_OOM, "autotune state copy");
+    }
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaMemcpyAsync(save, c->d_m, c->count * 8, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(save + c->count, c->d_s, c->count * 8, cudaMemcpyDeviceToDevice, st);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    auto trial = [&](const rsaprng_config &cfg, float *ms) -> int {
+        rsaprng_plan *p = nullptr;
+        int rc = plan_create_cfg(c, cfg, nreq, ids, counts, offs.data(), &p);
+        if (rc)
+            return rc;
+        rc = launch_plan(c, cfg, p->dp, d_r, nullptr, st, nullptr);  // warm-up
+        cudaEventRecord(a, st);
+        for (int r = 0; r < reps && rc == RSAPRNG_OK; r++)
+            rc = launch_plan(c, cfg, p->dp, d_r, nullptr, st, nullptr);
+        cudaEventRecord(b, st);
+        cudaError_t ee = cudaEventSynchronize(b);
+        cudaEventElapsedTime(ms, a, b);
+        cudaMemcpyAsync(c->d_m, save, c->count * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(c->d_s, save + c->count, c->count * 8, cudaMemcpyDeviceToDevice, st);
+        cudaStreamSynchronize(st);
+        rsaprng_plan_destroy(p);
+        if (rc == RSAPRNG_OK && ee != cudaSuccess)
+            rc = cuda_fail(ee, "autotune trial");
+        return rc;
+    };
+    rsaprng_config best = c->cfg;
+    float best_ms = 1e30f;
+    int rc = RSAPRNG_OK;
+    // Stage 1: routes at the default tiling. Stage 2: tilings for the best route.
+    const int routes[4][2] = {{RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT},
+                              {RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_FP64},
+                              {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_INT},
+                              {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_FP64}};
+    for (auto &rt : routes) {
+        rsaprng_config cfg = c->cfg;
+        cfg.modexp = rt[0];
+        cfg.divide = rt[1];
+        float ms;
+        if ((rc = trial(cfg, &ms)) != RSAPRNG_OK)
+            break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cfg;
+        }
+    }
+    const int tiles[][2] = {{128, 4}, {128, 8}, {256, 2}, {256, 4}, {256, 8}, {512, 2}, {512, 4}};
+    for (auto &tl : tiles) {
+        if (rc)
+            break;
+        rsaprng_config cfg = best;
+        cfg.threads_per_block = tl[0];
+        cfg.numbers_per_thread = tl[1];
+        float ms;
+        if ((rc = trial(cfg, &ms)) != RSAPRNG_OK)
+            break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cfg;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(st);
+    cudaFree(save);
+    cudaFree(d_r);
+    if (rc)
+        return rc;
+    c->cfg = best;
+    if (chosen)
+        *chosen = best;
+    return RSAPRNG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,387 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit-exact.
+
+Every integer output c_k and every double r_k must equal the oracle's bit for
+bit (the tolerance is zero: all integer steps are exact and the one floating
+point step is a correctly rounded IEEE division).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1811_11629_gb300 as R  # noqa: E402
+
+A = R.DEFAULT_ROOT
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+def seeded(ctx, O, master, k, rule=R.E_SMALLEST, lo=3, hi=3):
+    """k instances from workload seeds; returns ids and the oracle's parameters."""
+    seeds = workload.instance_seeds(master, k)
+    first = ctx.create_seeded(seeds, rule, lo, hi)
+    ids = np.arange(first, first + k, dtype=np.uint32)
+    par = []
+    for i, s in enumerate(seeds):
+        p, q, e, ms = O.params_from_seed(int(s), rule, lo, hi)
+        assert ctx.params(int(ids[i])) == (p, q, e, A)
+        par.append((p, q, e, ms % (p * q)))
+    return ids, par
+
+
+def check_stream(O, prm, m0, s0, got_c, got_r, a=A):
+    p, q, e = prm[:3]
+    if got_c is not None:
+        got_c = np.asarray(got_c).view(np.uint64)
+    n = len(got_c) if got_c is not None else len(got_r)
+    c, r, m1, s1 = O.generate(p, q, e, m0, s0, n, a=a)
+    if got_c is not None:
+        bad = np.nonzero(got_c != c)[0]
+        assert len(bad) == 0, f"c mismatch at {bad[:5]} (of {n})"
+    if got_r is not None:
+        bad = np.nonzero(bits(got_r) != bits(r))[0]
+        assert len(bad) == 0, f"r mismatch at {bad[:5]} (of {n})"
+    return m1, s1
+
+
+def test_plain_one_instance_1e6_full(O):
+    """Plain method: 1 instance, 1e6 outputs as uint64 c_k and float64 r_k."""
+    ctx = R.Context(4)
+    ids, par = seeded(ctx, O, master=1, k=1)
+    N = 1_000_000
+    c = torch.empty(N, dtype=torch.int64, device="cuda")
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.generate_both(int(ids[0]), N, c, r)
+    torch.cuda.synchronize()
+    m1, s1 = check_stream(O, par[0], par[0][3], 1, c.cpu().numpy(), r.cpu().numpy())
+    assert ctx.get_state(int(ids[0])) == (m1, s1)
+    # the next call continues the stream
+    ctx.generate_both(int(ids[0]), 777, c[:777], r[:777])
+    torch.cuda.synchronize()
+    check_stream(O, par[0], m1, s1, c[:777].cpu().numpy(), r[:777].cpu().numpy())
+
+
+ROUTES = [(R.MODEXP_CRT32, R.DIVIDE_INT), (R.MODEXP_CRT32, R.DIVIDE_FP64),
+          (R.MODEXP_MONT64, R.DIVIDE_INT), (R.MODEXP_MONT64, R.DIVIDE_FP64)]
+TILES = [(128, 2), (128, 8), (256, 4), (512, 2), (512, 8), (256, 8)]
+
+
+@pytest.mark.parametrize("modexp,divide", ROUTES)
+@pytest.mark.parametrize("threads,L", TILES)
+def test_routes_and_tilings_ragged(O, modexp, divide, threads, L):
+    """Every route and tiling, ragged counts (0, 1, tile-1, tile, tile+1, ...), two calls."""
+    ctx = R.Context(16, modexp=modexp, divide=divide, threads_per_block=threads,
+                    numbers_per_thread=L, chunk=1 << 20)
+    ids, par = seeded(ctx, O, master=11, k=8, rule=R.E_UNIFORM, lo=3, hi=65537)
+    tile = threads * L
+    counts = np.array([0, 1, 2, tile - 1, tile, tile + 1, 3 * tile + 5, 20011], np.uint64)
+    states = [(pr[3], 1) for pr in par]
+    for call in range(2):
+        total = int(counts.sum())
+        out_c = torch.full((total + 1,), 7, dtype=torch.int64, device="cuda")
+        out_r = torch.full((total + 1,), -1.0, dtype=torch.float64, device="cuda")
+        ctx.generate_batch(ids, counts, out_r=out_r, out_c=out_c)
+        torch.cuda.synchronize()
+        gc, gr = out_c.cpu().numpy().view(np.uint64), out_r.cpu().numpy()
+        assert gc[total] == 7 and gr[total] == -1.0  # nothing written past the end
+        off = 0
+        for i in range(len(ids)):
+            n = int(counts[i])
+            states[i] = check_stream(O, par[i], *states[i], gc[off:off + n], gr[off:off + n])
+            assert ctx.get_state(int(ids[i])) == states[i]
+            off += n
+
+
+def test_chunked_streams_and_fifo_requests(O):
+    """Long streams cut into chunks (skip-sum pre-pass) and several requests per instance."""
+    ctx = R.Context(8, chunk=4096 * 3, threads_per_block=256, numbers_per_thread=4)
+    ids, par = seeded(ctx, O, master=12, k=3, rule=R.E_UNIFORM, lo=3, hi=257)
+    a, b, c = (int(x) for x in ids)
+    req_ids = np.array([a, b, a, c, a, b], np.uint32)
+    counts = np.array([50000, 7, 12289, 100003, 1, 40000], np.uint64)
+    # scattered, non-overlapping output offsets
+    offsets = np.array([300000, 0, 100, 150000, 299990, 50000], np.uint64)
+    out = torch.full((400000,), -1.0, dtype=torch.float64, device="cuda")
+    ctx.generate_batch(req_ids, counts, out_r=out, offsets=offsets)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    st = {a: (par[0][3], 1), b: (par[1][3], 1), c: (par[2][3], 1)}
+    pmap = {a: par[0], b: par[1], c: par[2]}
+    for i in range(len(req_ids)):  # array order = stream order per instance
+        iid, n, o = int(req_ids[i]), int(counts[i]), int(offsets[i])
+        st[iid] = check_stream(O, pmap[iid], *st[iid], None, g[o:o + n])
+    for iid in (a, b, c):
+        assert ctx.get_state(iid) == st[iid]
+
+
+def test_single_instance_chunked_long(O):
+    ctx = R.Context(2, chunk=8192)
+    ids, par = seeded(ctx, O, master=13, k=1, rule=R.E_AT_LEAST, lo=17, hi=17)
+    N = 3_000_017
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.generate_f64(int(ids[0]), N, r)
+    torch.cuda.synchronize()
+    m1, s1 = check_stream(O, par[0], par[0][3], 1, None, r.cpu().numpy())
+    assert ctx.get_state(int(ids[0])) == (m1, s1)
+
+
+def test_checkpoint_resume(O):
+    """Sec. IV state {m, s}: generate N, save, generate M; restore, generate M again."""
+    ctx = R.Context(4)
+    ids, par = seeded(ctx, O, master=14, k=1, rule=R.E_UNIFORM, lo=3, hi=65537)
+    i = int(ids[0])
+    x = torch.empty(50000, dtype=torch.int64, device="cuda")
+    ctx.generate_u64(i, 12345, x)
+    saved = ctx.get_state(i)
+    y1 = torch.empty(30000, dtype=torch.int64, device="cuda")
+    y2 = torch.empty(30000, dtype=torch.int64, device="cuda")
+    ctx.generate_u64(i, 30000, y1)
+    ctx.set_state(i, *saved)
+    ctx.generate_u64(i, 30000, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    whole = torch.empty(42345, dtype=torch.int64, device="cuda")
+    ctx.set_state(i, par[0][3], 1)
+    ctx.generate_u64(i, 42345, whole)
+    torch.cuda.synchronize()
+    assert torch.equal(whole[:12345], x[:12345]) and torch.equal(whole[12345:], y1)
+    with pytest.raises(R.RsaPrngError):
+        ctx.set_state(i, par[0][0] * par[0][1], 1)  # m >= n
+    with pytest.raises(R.RsaPrngError):
+        ctx.set_state(i, 0, 0)  # s = 0
+
+
+def test_split_substreams(O):
+    """Sec. VI: child gamma keeps m and starts at s a^(gamma floor((Q-1)/Mv))."""
+    ctx = R.Context(64)
+    ids, par = seeded(ctx, O, master=15, k=1)
+    parent = int(ids[0])
+    tmp = torch.empty(1000, dtype=torch.int64, device="cuda")
+    ctx.generate_u64(parent, 1000, tmp)  # split from a non-initial state
+    m, s = ctx.get_state(parent)
+    kids = ctx.split(parent, 32)
+    assert ctx.get_state(parent) == (m, s)
+    n = 5000
+    counts = np.full(32, n, np.uint64)
+    oc = torch.empty(32 * n, dtype=torch.int64, device="cuda")
+    orr = torch.empty(32 * n, dtype=torch.float64, device="cuda")
+    ctx.generate_batch(kids, counts, out_r=orr, out_c=oc)
+    torch.cuda.synchronize()
+    gc, gr = oc.cpu().numpy().view(np.uint64), orr.cpu().numpy()
+    for g in range(32):
+        s_g = O.split_s0(s, A, 32, g)
+        check_stream(O, par[0], m, s_g, gc[g * n:(g + 1) * n], gr[g * n:(g + 1) * n])
+    # child 0 continues the parent's own stream
+    pc = torch.empty(n, dtype=torch.int64, device="cuda")
+    ctx.generate_u64(parent, n, pc)
+    torch.cuda.synchronize()
+    assert np.array_equal(pc.cpu().numpy().view(np.uint64), gc[:n].view(np.uint64))
+
+
+def test_cribs_and_one_guard(O):
+    """Sec. IV cribs 0, 1, n-1 and the r = 1.0 guard of Sec. V through the full path."""
+    ctx = R.Context(8)
+    p, q, e, _ = O.params_from_seed(int(workload.instance_seeds(16, 1)[0]))
+    n = p * q
+    for target, want_r in ((0, 0.0), (1, None), (n - 1, 1.0 - 2.0**-53)):
+        m0 = (target - A) % n  # s_1 = a (s_0 = 1), so m_1 = target
+        i = ctx.create_ex(p, q, e, A, m0, 1)
+        c = torch.empty(3, dtype=torch.int64, device="cuda")
+        r = torch.empty(3, dtype=torch.float64, device="cuda")
+        ctx.generate_both(i, 3, c, r)
+        torch.cuda.synchronize()
+        assert int(c[0]) == target
+        if want_r is not None:
+            assert float(r[0]) == want_r
+        check_stream(O, (p, q, e), m0, 1, c.cpu().numpy(), r.cpu().numpy())
+
+
+@pytest.mark.parametrize("divide", [R.DIVIDE_INT, R.DIVIDE_FP64])
+def test_unit_step_random_and_edges(O, divide):
+    """The output step alone on chosen ciphertexts: random, near n, below 2^53, ties."""
+    ctx = R.Context(8)
+    ids, par = seeded(ctx, O, master=17, k=4)
+    rng = np.random.default_rng(3)
+    for i, (p, q, e, _) in zip(ids, par):
+        n = p * q
+        cs = [rng.integers(0, n, 400000, dtype=np.uint64)]
+        cs.append(np.uint64(n) - rng.integers(1, 1 << 14, 20000, dtype=np.uint64))
+        cs.append(rng.integers(0, 1 << 54, 20000, dtype=np.uint64))
+        edge = [0, 1, 2, (1 << 53) - 1, 1 << 53, (1 << 53) + 1, (1 << 62) - 1, 1 << 62, n - 1,
+                n - 2, n >> 1]
+        # values whose conversion to double is an exact tie (ties to even), all bit lengths
+        for bl in range(54, n.bit_length() + 1):
+            for mant in rng.integers(1 << 52, 1 << 53, 64):
+                x = (int(mant) << (bl - 53)) | (1 << (bl - 54))
+                if x < n:
+                    edge.append(x)
+        cs.append(np.array(edge, np.uint64))
+        c = np.concatenate(cs)
+        dc = torch.from_numpy(c.view(np.int64)).cuda().view(torch.uint64)
+        dr = torch.empty(len(c), dtype=torch.float64, device="cuda")
+        assert ctx.L.rsaprng_unit_f64(ctx.h, int(i), len(c), dc.data_ptr(), dr.data_ptr(),
+                                      divide, torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        want = O.unit_many(c, n)
+        got = dr.cpu().numpy()
+        bad = np.nonzero(bits(got) != bits(want))[0]
+        assert len(bad) == 0, f"n={n}: c={c[bad[:3]]} got={got[bad[:3]]} want={want[bad[:3]]}"
+        assert (got < 1.0).all() and (got >= 0.0).all()
+
+
+def test_large_exponents(O):
+    """Exponents up to 2^32 - 1 exercise the top-bit handling of the square-and-multiply loop."""
+    ctx = R.Context(16)
+    p, q, _, ms = O.params_from_seed(int(workload.instance_seeds(18, 1)[0]))
+    phi = (p - 1) * (q - 1)
+    es = [e for e in (3, 5, 7, 65537, 65539, (1 << 31) + 11, (1 << 32) - 1, (1 << 32) - 3,
+                      2**31 - 1, 1 << 31 | 1, 0xAAAAAAAB, 0x80000001) if e % 2 and
+          math.gcd(e, phi) == 1]
+    assert len(es) >= 5
+    for modexp in (R.MODEXP_CRT32, R.MODEXP_MONT64):
+        ctx.configure(modexp=modexp)
+        for e in es:
+            i = ctx.create(p, q, e, ms)
+            c = torch.empty(3000, dtype=torch.int64, device="cuda")
+            r = torch.empty(3000, dtype=torch.float64, device="cuda")
+            ctx.generate_both(i, 3000, c, r)
+            torch.cuda.synchronize()
+            check_stream(O, (p, q, e), ms % (p * q), 1, c.cpu().numpy(), r.cpu().numpy())
+
+
+def test_all_roots(O):
+    """Every allowed skip multiplier (restricted primitive roots and the small roots)."""
+    ctx = R.Context(32)
+    p, q, e, ms = O.params_from_seed(int(workload.instance_seeds(19, 1)[0]))
+    roots = [2307085864, 3157107955, 3200261722, 3211103532, 3338736601, 3423977237,
+             3465965455, 3474009732, 3512424704, 3, 6, 7, 10, 11]
+    ids = [ctx.create_ex(p, q, e, a, ms % (p * q), 12345) for a in roots]
+    n = 10000
+    out = torch.empty(len(ids) * n, dtype=torch.int64, device="cuda")
+    ctx.generate_batch(np.array(ids, np.uint32), np.full(len(ids), n, np.uint64), out_c=out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    for k, a in enumerate(roots):
+        check_stream(O, (p, q, e), ms % (p * q), 12345, g[k * n:(k + 1) * n], None, a=a)
+    with pytest.raises(R.RsaPrngError):
+        ctx.create_ex(p, q, e, 3163786287, 0, 1)  # listed but not a primitive root
+
+
+def test_plan_graph_replay(O):
+    """A plan captured in a CUDA graph: each replay generates the next outputs."""
+    ctx = R.Context(64)
+    ids, par = seeded(ctx, O, master=20, k=40, rule=R.E_UNIFORM, lo=3, hi=257)
+    counts = workload.lognormal_lengths(20, 40, median=3000.0, sigma=1.0, lo=1, hi=50000)
+    total = int(counts.sum())
+    plan = ctx.plan(ids, counts)
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    plan.capture(out_r=out, stream=s)
+    states = [(pr[3], 1) for pr in par]
+    for rep in range(2):
+        plan.replay(stream=s)
+        s.synchronize()
+        g = out.cpu().numpy()
+        off = 0
+        for i in range(len(ids)):
+            n = int(counts[i])
+            states[i] = check_stream(O, par[i], *states[i], None, g[off:off + n])
+            off += n
+    info = plan.info()
+    assert info["numbers"] == total and info["launches"] >= 1
+    plan.close()
+
+
+def test_autotune_bit_identical_and_state_preserved(O):
+    ctx = R.Context(64)
+    ids, par = seeded(ctx, O, master=21, k=24, rule=R.E_UNIFORM, lo=3, hi=65537)
+    counts = np.full(len(ids), 20000, np.uint64)
+    before = [ctx.get_state(int(i)) for i in ids]
+    chosen = ctx.autotune(ids, counts, reps=1)
+    assert [ctx.get_state(int(i)) for i in ids] == before
+    assert chosen["threads_per_block"] in (128, 256, 512)
+    out = torch.empty(int(counts.sum()), dtype=torch.float64, device="cuda")
+    ctx.generate_batch(ids, counts, out_r=out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    for i in range(len(ids)):
+        check_stream(O, par[i], par[i][3], 1, None, g[i * 20000:(i + 1) * 20000])
+
+
+def test_generate_batch_host_equals_device(O):
+    """End-to-end form: outputs land in host memory; same numbers as the device form."""
+    ctx = R.Context(32)
+    ids, par = seeded(ctx, O, master=22, k=20, rule=R.E_UNIFORM, lo=3, hi=257)
+    counts = np.array([1 << 18] * 10 + [12345] * 10, np.uint64)
+    total = int(counts.sum())
+    h_r = torch.empty(total, dtype=torch.float64).pin_memory()
+    h_c = np.empty(total, np.uint64)
+    ctx.generate_batch_host(ids, counts, h_r=h_r, h_c=h_c)
+    g = h_r.numpy()
+    off = 0
+    for i in range(len(ids)):
+        n = int(counts[i])
+        check_stream(O, par[i], par[i][3], 1, h_c[off:off + n], g[off:off + n])
+        off += n
+
+
+def test_microbenchmarks_run():
+    ctx = R.Context(1)
+    assert ctx.microbench(0) > 100.0  # G IMAD lane-ops/s
+    assert ctx.microbench(1) > 1.0  # G double divisions/s
+    assert ctx.microbench(2, 1 << 30) > 500.0  # GB/s
+
+
+def test_bulk_full_size_sampled(O):
+    """Plain bulk at full size (1024 instances x 2^20 float64, one instance per block, 8 GiB)
+    in the launch configuration the benchmark times; 8 instances compared in full, every
+    instance at sampled indices, and every end state."""
+    cfg = workload.CONFIGS["bulk_1024x2^20"]
+    k, n = cfg["instances"], cfg["count"]
+    ctx = R.Context(k, chunk=n)
+    seeds = workload.instance_seeds(cfg["master"], k)
+    first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    ids = np.arange(first, first + k, dtype=np.uint32)
+    plan = ctx.plan(ids, np.full(k, n, np.uint64))
+    out = torch.empty(k * n, dtype=torch.float64, device="cuda")
+    plan.launch(out_r=out)
+    torch.cuda.synchronize()
+    par = [O.params_from_seed(int(s), cfg["e_rule"], cfg["e_lo"], cfg["e_hi"]) for s in seeds]
+    p = np.array([x[0] for x in par], np.uint64)
+    q = np.array([x[1] for x in par], np.uint64)
+    e = np.array([x[2] for x in par], np.uint64)
+    m0 = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
+    rng = np.random.default_rng(5)
+    ks = [np.unique(np.concatenate([[1, 2, n], rng.integers(1, n + 1, 29)])) for _ in range(k)]
+    m = m0.copy()
+    s = np.ones(k, np.uint64)
+    _, want_r = O.sample_many(p, q, e, np.full(k, A, np.uint64), m, s, ks)
+    idx = np.concatenate([i * n + kk - 1 for i, kk in enumerate(ks)]).astype(np.int64)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(bits(got), bits(want_r))
+    # end state of every instance = oracle after n outputs (m, s were advanced to k = n)
+    for i in range(k):
+        assert ctx.get_state(int(ids[i])) == (int(m[i]), int(s[i])), i
+    full = [0, 1, 511, 1023, 100, 200, 300, 400]
+    g = out.view(k, n)[full].cpu().numpy()
+    for j, i in enumerate(full):
+        check_stream(O, par[i][:3], int(m0[i]), 1, None, g[j])
+    plan.close()

@@ -1,0 +1,91 @@
+"""Host-side checks that need no GPU: the library loads and exports its ABI,
+and its host parameter layer agrees with the oracle."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "rsaprng.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsaprng_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1811_11629_gb300 as R
+
+    R._lib.load()
+    return R
+
+
+def test_library_exports_every_declared_symbol(R):
+    L = R._lib.load()
+    declared = _declared_symbols()
+    assert len(declared) >= 40
+    for name in declared:
+        assert hasattr(L, name), name
+    # and the binding covers the same set
+    assert set(declared) == set(R._lib.SIGNATURES), set(declared) ^ set(R._lib.SIGNATURES)
+
+
+def test_strerror_covers_codes(R):
+    L = R._lib.load()
+    for code in list(R._lib.ERRORS) + [0]:
+        msg = L.rsaprng_strerror(code).decode()
+        assert msg and msg != "unknown error"
+
+
+def test_is_prime_matches_oracle(R, oracle_mod):
+    rng = np.random.default_rng(1)
+    xs = list(rng.integers(1 << 31, 1 << 32, 20000, dtype=np.uint64))
+    xs += list(rng.integers(1, 1 << 63, 2000, dtype=np.uint64))
+    xs += [2, 3, 4, 2047, 3215031751, 2152302898747, 3825123056546413051, (1 << 63) - 25,
+           (1 << 61) - 1, (1 << 64) - 59]
+    for x in xs:
+        assert R.is_prime(int(x)) == oracle_mod.is_prime(int(x)), int(x)
+
+
+@pytest.mark.parametrize("rule,lo,hi", [(0, 3, 3), (1, 3, 65537), (1, 3, 257), (2, 3, 3),
+                                        (2, 65537, 65537)])
+def test_params_from_seed_matches_oracle(R, oracle_mod, rule, lo, hi):
+    for s in workload.instance_seeds(1234 + rule, 300):
+        assert R.params_from_seed(int(s), rule, lo, hi) == \
+            oracle_mod.params_from_seed(int(s), rule, lo, hi)
+
+
+def test_allowed_roots(R):
+    listed = [2307085864, 3157107955, 3200261722, 3211103532, 3338736601, 3423977237,
+              3465965455, 3474009732, 3512424704, 3, 6, 7, 10, 11]
+    for a in listed:
+        assert R.root_allowed(a)
+    for a in [3163786287, 2, 4, 5, 12, 2307085865, 0, 1]:
+        assert not R.root_allowed(a)
+
+
+def test_parameter_validation_codes(R):
+    """Fault injection on the host: bad primes, ranges, equal primes, bad exponents."""
+    C = R._lib.CODES
+    p, q = 4294967291, 4294967279  # the two largest primes below 2^32
+    assert R.validate_params(p, q, 3) in (0, C["ERR_E"])
+    e_ok = next(e for e in range(3, 200, 2) if math.gcd(e, (p - 1) * (q - 1)) == 1)
+    assert R.validate_params(p, q, e_ok) == 0
+    assert R.validate_params(p, p, e_ok) == C["ERR_P_EQ_Q"]
+    assert R.validate_params(p, 4294967295, e_ok) == C["ERR_NOT_PRIME"]
+    assert R.validate_params(p, 65521, e_ok) == C["ERR_RANGE"]
+    assert R.validate_params(1 << 32, q, e_ok) == C["ERR_RANGE"]
+    assert R.validate_params(p, q, e_ok + 1) == C["ERR_E"]
+    assert R.validate_params(p, q, 1) == C["ERR_E"]
+    bad_e = next(e for e in range(3, 2000, 2) if math.gcd(e, (p - 1) * (q - 1)) != 1)
+    assert R.validate_params(p, q, bad_e) == C["ERR_E"]
+    # a prime whose (p-1)/2 is composite fails the safe-prime rule of Sec. V
+    assert not R.is_prime((p - 1) // 2) or not R.is_prime((q - 1) // 2)
+    assert R.validate_params(p, q, e_ok, require_safe=True) == C["ERR_NOT_PRIME"]
