@@ -51,6 +51,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="override the instance count (small profiling runs only)")
+    ap.add_argument("--count", type=int, default=0,
+                    help="override numbers per instance (small profiling runs only)")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--per-thread", type=int, default=0)
+    ap.add_argument("--modexp", type=int, default=0)
+    ap.add_argument("--divide", type=int, default=0)
     return ap.parse_args(argv)
 
 
@@ -195,7 +203,7 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
 
     oracle.build()
     threads = oracle.max_threads()
-    k = min(len(seeds), max(threads * 4, 64))
+    k = len(seeds)
     par = [oracle.params_from_seed(int(s), cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
            for s in seeds[:k]]
     p = np.array([x[0] for x in par], np.uint64)
@@ -211,13 +219,13 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
                              route=oracle.ROUTE_PAPER, want_c=False, want_r=True)
         return time.perf_counter() - t0
 
-    pilot_n = 2048
+    pilot_n = 1024
     dt = run(pilot_n)
     n = int(min(cfg["count"], max(pilot_n, pilot_n * target_s / max(dt, 1e-3))))
     dt = run(n)
     return {"value": k * n / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {k} of {len(seeds)} instances x {n} numbers (of {cfg['count']}), "
-                      f"route=paper (Schrage + CRT), {dt:.1f} s"}
+            "sample": f"all {k} instances x first {n} numbers (of {cfg['count']}) each, "
+                      f"route=paper (Schrage + CRT), {dt:.1f} s wall"}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -228,10 +236,17 @@ def run_ours(args) -> int:
 
     dist = Dist(backend_gpu=True)
     torch.cuda.set_device(dist.local_rank)
-    cfg = workload.CONFIGS[WORKLOAD]
+    cfg = dict(workload.CONFIGS[WORKLOAD])
+    if args.instances:
+        cfg["instances"] = args.instances
+    if args.count:
+        cfg["count"] = args.count
     k, n = cfg["instances"], cfg["count"]
     seeds = rank_seeds(cfg, dist.rank)
-    ctx = R.Context(k, device=dist.local_rank, chunk=n)
+    knobs = {x: y for x, y in (("threads_per_block", args.threads),
+                               ("numbers_per_thread", args.per_thread),
+                               ("modexp", args.modexp), ("divide", args.divide)) if y}
+    ctx = R.Context(k, device=dist.local_rank, chunk=n, **knobs)
     first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
     counts = np.full(k, n, np.uint64)
@@ -312,6 +327,9 @@ def run_ours(args) -> int:
     cur = ctx.config()
     result["config"]["kernel"] = {x: cur[x] for x in ("modexp", "divide", "threads_per_block",
                                                       "numbers_per_thread")}
+    result["config"]["kernel"].update(plan.shape())
+    if (k, n) != (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]):
+        result["config"]["workload"] = f"bulk_{k}x{n} (reduced size, not the benchmark workload)"
     del out
     torch.cuda.empty_cache()
 

@@ -196,6 +196,11 @@ int rsaprng_plan_replay(rsaprng_plan *plan, void *stream);
 /* Kernel launches one rsaprng_plan_launch makes, and numbers it generates. */
 int rsaprng_plan_info(const rsaprng_plan *plan, uint64_t *launches, uint64_t *numbers,
                       uint64_t *chunks);
+/* Shape of the plan's most recent generation launch: grid blocks, threads
+ * per block, resident blocks per SM, and whether blocks pull work items from
+ * a queue (1) or take one each (0). Zeros before the first launch. */
+int rsaprng_plan_shape(const rsaprng_plan *plan, int *grid, int *threads, int *blocks_per_sm,
+                       int *persistent);
 void rsaprng_plan_destroy(rsaprng_plan *plan);
 
 /* --------------------------------------------------------------- tuning */
@@ -236,12 +241,22 @@ int rsaprng_server_wait(rsaprng_server *srv, uint64_t ticket, uint64_t timeout_n
 /* Device address of a completed ticket's outputs (valid until released). */
 int rsaprng_server_result(rsaprng_server *srv, uint64_t ticket, const double **d_r,
                           uint64_t *count);
-/* Copies a completed ticket's outputs to d_dst (count doubles) on `stream`. */
+/* Copies a completed ticket's outputs to d_dst (count doubles) on `stream`;
+ * release the ticket only after that copy has completed. */
 int rsaprng_server_copy(rsaprng_server *srv, uint64_t ticket, double *d_dst, void *stream);
 int rsaprng_server_release(rsaprng_server *srv, uint64_t ticket);
 /* Cancels a ticket that has not been admitted yet. */
 int rsaprng_server_cancel(rsaprng_server *srv, uint64_t ticket);
 int rsaprng_server_stats(rsaprng_server *srv, rsaprng_stats *out);
+/* Open-loop trace replay for load measurements on an idle server: request i
+ * (instance ids[i], counts[i] numbers) is submitted arrival_ns[i] ns after the
+ * call starts, and its outputs are released as soon as they complete.
+ * Returns when all n requests are done (RSAPRNG_ERR_TIMEOUT after timeout_ns).
+ * Latencies in ms (arrival to completion) go to lat_ms_out[i] if not NULL, in
+ * completion order; rsaprng_server_stats then reports this replay alone. */
+int rsaprng_server_replay(rsaprng_server *srv, uint64_t n, const rsaprng_id *ids,
+                          const uint64_t *counts, const uint64_t *arrival_ns,
+                          uint64_t timeout_ns, double *lat_ms_out);
 void rsaprng_server_destroy(rsaprng_server *srv);
 
 /* ------------------------------------------------------- host utilities */

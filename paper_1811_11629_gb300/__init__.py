@@ -259,6 +259,11 @@ class Plan:
               "plan_info")
         return {"launches": a.value, "numbers": b.value, "chunks": c.value}
 
+    def shape(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        check(self.L.rsaprng_plan_shape(self.h, *[ctypes.byref(x) for x in v]), "plan_shape")
+        return dict(zip(("grid", "threads", "blocks_per_sm", "persistent"), (x.value for x in v)))
+
     def close(self):
         if self.h:
             self.L.rsaprng_plan_destroy(self.h)
@@ -316,8 +321,11 @@ class Server:
 
         _, n = self.result_ptr(ticket)
         out = torch.empty(n, dtype=torch.float64, device="cuda")
-        check(self.L.rsaprng_server_copy(self.h, ticket, _dptr(out) if n else None,
-                                         _stream_ptr(stream)), "server_copy")
+        st = _stream_ptr(stream)
+        check(self.L.rsaprng_server_copy(self.h, ticket, _dptr(out) if n else None, st),
+              "server_copy")
+        # the copy must finish before the ticket is released and its arena reused
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         return out
 
     def release(self, ticket: int):
@@ -330,6 +338,17 @@ class Server:
         s = Stats()
         check(self.L.rsaprng_server_stats(self.h, ctypes.byref(s)), "server_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def replay(self, ids, counts, arrival_s, timeout_s: float = 600.0):
+        """Open-loop replay of a request trace (native load generator); returns latencies."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        arr = np.ascontiguousarray(np.round(np.asarray(arrival_s) * 1e9), dtype=np.uint64)
+        lat = np.zeros(len(ids), np.float64)
+        check(self.L.rsaprng_server_replay(self.h, len(ids), _u32p(ids), _u64p(counts),
+                                           _u64p(arr), int(timeout_s * 1e9),
+                                           lat.ctypes.data_as(_lib.pdbl)), "server_replay")
+        return lat
 
     def close(self):
         if self.h:

@@ -74,6 +74,8 @@ SIGNATURES = {
     "rsaprng_plan_capture": (i32, [vp, vp, vp, vp]),
     "rsaprng_plan_replay": (i32, [vp, vp]),
     "rsaprng_plan_info": (i32, [vp, pu64, pu64, pu64]),
+    "rsaprng_plan_shape": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     "rsaprng_plan_destroy": (None, [vp]),
     "rsaprng_autotune": (i32, [vp, u64, pu32, pu64, i32, ctypes.POINTER(Config)]),
     "rsaprng_server_create": (i32, [vp, u64, i32, pvp]),
@@ -85,6 +87,7 @@ SIGNATURES = {
     "rsaprng_server_release": (i32, [vp, u64]),
     "rsaprng_server_cancel": (i32, [vp, u64]),
     "rsaprng_server_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+    "rsaprng_server_replay": (i32, [vp, u64, pu32, pu64, pu64, u64, pdbl]),
     "rsaprng_server_destroy": (None, [vp]),
     "rsaprng_is_prime": (i32, [u64]),
     "rsaprng_root_allowed": (i32, [u64]),

@@ -90,7 +90,7 @@ DeviceTables ctx_tables(rsaprng_ctx *c)
 }
 
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
-                     bool want_c)
+                     bool want_c, int *occupancy)
 {
     GenLaunch g;
     g.threads = cfg.threads_per_block;
@@ -98,9 +98,23 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
     g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64 : DIVIDE_INT;
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
-    int occ = gen_blocks_per_sm(g, smem);
+    // Occupancy queries cost microseconds; cache them per kernel and smem size.
+    const int ti = g.threads / 128 - 1 < 0 ? 0 : (g.threads / 128 - 1 > 3 ? 3 : g.threads / 128 - 1);
+    const int li = g.L == 2 ? 0 : (g.L == 4 ? 1 : 2);
+    int &cached = c->occ_cache[ti][li][g.modexp - 1][g.divide - 1];
+    size_t &cached_smem = c->occ_smem[ti][li][g.modexp - 1][g.divide - 1];
+    int occ;
+    if (cached > 0 && cached_smem == smem) {
+        occ = cached;
+    } else {
+        occ = gen_blocks_per_sm(g, smem);
+        cached = occ;
+        cached_smem = smem;
+    }
     if (occ < 1)
         occ = 1;
+    if (occupancy)
+        *occupancy = occ;
     if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ)
         occ = cfg.blocks_per_sm;
     const uint64_t resident = (uint64_t)occ * c->sms;
@@ -299,7 +313,8 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         nl += 2;
     }
     if (dp.nitems) {
-        GenLaunch g = ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr);
+        GenLaunch g = ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
+        dp.last = g;
         if (g.persistent) {
             if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
                 return cuda_fail(e, "ticket reset");
@@ -439,6 +454,8 @@ int rsaprng_ctx_create(rsaprng_ctx **out, int device, uint64_t max_instances,
     c->device = device;
     c->cfg = conf;
     c->capacity = max_instances;
+    memset(c->occ_cache, 0, sizeof c->occ_cache);
+    memset(c->occ_smem, 0, sizeof c->occ_smem);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     auto cleanup = [&](int code) {
         rsaprng_ctx_destroy(c);

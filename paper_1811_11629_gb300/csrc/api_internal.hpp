@@ -36,6 +36,8 @@ struct DevPlan {
     uint64_t *chunk_s = nullptr;
     uint32_t nitems = 0, nchunks = 0, ngroups = 0;
     uint64_t numbers = 0;
+    GenLaunch last{};  // shape of the most recent generation launch
+    int occupancy = 0; // resident blocks per SM of that launch
 };
 
 constexpr int kScratchSlots = 4;
@@ -59,6 +61,8 @@ struct rsaprng_ctx {
     rsaprng::ScratchSlot slots[rsaprng::kScratchSlots];
     int next_slot = 0;
     uint64_t launches = 0;
+    int occ_cache[4][3][2][2];  // blocks/SM by (threads/128-1, L index, modexp, divide), -1 unknown
+    size_t occ_smem[4][3][2][2];
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
 };
@@ -69,7 +73,7 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 DeviceTables ctx_tables(rsaprng_ctx *c);
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
-                     bool want_c);
+                     bool want_c, int *occupancy = nullptr);
 int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
                const uint64_t *offsets, uint64_t chunk, HostPlan &hp);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);

@@ -137,6 +137,22 @@ int rsaprng_plan_info(const rsaprng_plan *p, uint64_t *launches, uint64_t *numbe
     return RSAPRNG_OK;
 }
 
+int rsaprng_plan_shape(const rsaprng_plan *p, int *grid, int *threads, int *blocks_per_sm,
+                       int *persistent)
+{
+    if (!p)
+        return fail(RSAPRNG_ERR_ARG, "null plan");
+    if (grid)
+        *grid = p->dp.last.grid;
+    if (threads)
+        *threads = p->dp.last.threads;
+    if (blocks_per_sm)
+        *blocks_per_sm = p->dp.occupancy;
+    if (persistent)
+        *persistent = p->dp.last.persistent ? 1 : 0;
+    return RSAPRNG_OK;
+}
+
 void rsaprng_plan_destroy(rsaprng_plan *p)
 {
     if (!p)
