@@ -164,6 +164,26 @@ int rsaprng_generate_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_
 int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
                           void *stream);
 
+/* The same as rsaprng_generate_f64, for callers that cannot allocate: code
+ * running inside a CUDA stream capture, latency-critical threads that forbid
+ * allocator calls, or hosts that give all device memory to their own pool.
+ * The paper has no counterpart; this is a deployment variant of the same
+ * path. It allocates nothing: its scratch (chunk list, skip sums, work-queue
+ * counter) is one fixed device array of about 330 KB inside the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *  - Limit: N <= 2^36 outputs (at most 4096 chunks of at most 2^24 outputs);
+ *    larger N returns RSAPRNG_ERR_ARG before anything is launched. Errors of
+ *    this call return their code without setting rsaprng_last_error_detail.
+ *  - The first call on a device looks up the array's device address (one
+ *    cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (the queue counter is cleared by every call). Calls whose kernels
+ *    overlap on the GPU (different streams, or contexts on the same device)
+ *    race on it: order them, e.g. on one stream.
+ * Output and state advance are identical to rsaprng_generate_f64. */
+int rsaprng_generate_f64_noalloc(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_r,
+                                 void *stream);
+
 /* Many requests in one launch sequence. Request i draws counts[i] outputs of
  * instance ids[i] into d_r/d_c at element offset out_offsets[i] (either
  * output may be NULL). ids, counts, out_offsets are HOST arrays. Requests of

@@ -67,6 +67,7 @@ SIGNATURES = {
     "rsaprng_generate_u64": (i32, [vp, u32, u64, vp, vp]),
     "rsaprng_generate_f64": (i32, [vp, u32, u64, vp, vp]),
     "rsaprng_generate_both": (i32, [vp, u32, u64, vp, vp, vp]),
+    "rsaprng_generate_f64_noalloc": (i32, [vp, u32, u64, vp, vp]),
     "rsaprng_generate_batch": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_generate_batch_host": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_plan_create": (i32, [vp, u64, pu32, pu64, pu64, pvp]),
