@@ -84,7 +84,9 @@ enum {
     RSAPRNG_DIVIDE_AUTO = 0,
     RSAPRNG_DIVIDE_INT = 1,   /* integer rounding + division by the invariant
                                  significand of RN(n) (Moller & Granlund 2011) */
-    RSAPRNG_DIVIDE_FP64 = 2   /* IEEE double conversion and division */
+    RSAPRNG_DIVIDE_FP64 = 2,  /* IEEE double conversion and division */
+    RSAPRNG_DIVIDE_HYBRID = 3 /* FP64 for three outputs in four, integer for the
+                                 fourth: keeps both the FP64 and integer pipes busy */
 };
 /* Exponent rules for rsaprng_params_from_seed. */
 enum { RSAPRNG_E_SMALLEST = 0, RSAPRNG_E_UNIFORM = 1, RSAPRNG_E_AT_LEAST = 2 };
@@ -321,7 +323,9 @@ uint64_t rsaprng_launch_count(const rsaprng_ctx *ctx);
 /* Device microbenchmarks for the roofline, timed with CUDA events on an
  * internal stream: kind 0 = 32-bit integer multiply-add issue rate
  * (result in G lane-ops/s), 1 = FP64 divide rate (G div/s), 2 = HBM write
- * bandwidth (GB/s) over `bytes` bytes. */
+ * bandwidth (GB/s) over `bytes` bytes, 3 = widening 32x32->64 multiply rate,
+ * 4 = 32-bit high-half multiply rate, 5 = 32-bit Montgomery product rate
+ * (3-5 in G per second). */
 int rsaprng_microbench(rsaprng_ctx *ctx, int kind, uint64_t bytes, double *result);
 
 const char *rsaprng_strerror(int code);

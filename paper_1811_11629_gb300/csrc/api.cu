@@ -39,12 +39,12 @@ int cuda_fail(cudaError_t e, const char *what)
 }
 
 static const rsaprng_config kDefaultConfig = {
-    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT, 256, 4, 0, 1ULL << 18, 0,
+    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT, 256, 8, 0, 1ULL << 18, 0,
     {0, 0, 0, 0, 0, 0, 0}};
 
 static int check_config(const rsaprng_config &c)
 {
-    if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 2)
+    if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 3)
         return fail(RSAPRNG_ERR_ARG, "config: modexp/divide out of range");
     if (c.threads_per_block && c.threads_per_block != 128 && c.threads_per_block != 256 &&
         c.threads_per_block != 512)
@@ -96,7 +96,9 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.threads = cfg.threads_per_block;
     g.L = cfg.numbers_per_thread;
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
-    g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64 : DIVIDE_INT;
+    g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64     ? DIVIDE_FP64
+               : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
+                                                     : DIVIDE_INT;
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
     // Occupancy queries cost microseconds; cache them per kernel and smem size.
     const int ti = g.threads / 128 - 1 < 0 ? 0 : (g.threads / 128 - 1 > 3 ? 3 : g.threads / 128 - 1);
@@ -802,7 +804,7 @@ int rsaprng_unit_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, const uint64_t *
         divide = c->cfg.divide;
     cudaSetDevice(c->device);
     cudaError_t e = launch_unit(ctx_tables(c), id, N, d_c, d_r,
-                                divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64 : DIVIDE_INT,
+                                divide == RSAPRNG_DIVIDE_INT ? DIVIDE_INT : DIVIDE_FP64,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "unit launch");
@@ -831,6 +833,8 @@ int rsaprng_microbench(rsaprng_ctx *c, int kind, uint64_t bytes, double *result)
             e = microbench_write(buf, bytes, result, st);
             cudaFree(buf);
         }
+    } else if (kind >= 3 && kind <= 5) {
+        e = microbench_mul(kind - 3, result, st);
     } else {
         cudaStreamDestroy(st);
         return fail(RSAPRNG_ERR_ARG, "unknown microbenchmark %d", kind);

@@ -160,10 +160,10 @@ __device__ __forceinline__ void encrypt_mont64(const u64 (&m)[L], u64 (&c)[L], c
 
 constexpr u64 ONE_MINUS_ULP_BITS = 0x3FEFFFFFFFFFFFFFULL;  // 1 - 2^-53
 
-// r = RN(RN(c)/RN(n)) with IEEE double conversion and division.
-__device__ __forceinline__ double unit_fp64(u64 c, u64 n)
+// r = RN(RN(c)/RN(n)) with IEEE double conversion and division; dn = RN(n).
+__device__ __forceinline__ double unit_fp64(u64 c, double dn)
 {
-    const double r = __ddiv_rn(__ull2double_rn(c), __ull2double_rn(n));
+    const double r = __ddiv_rn(__ull2double_rn(c), dn);
     return r >= 1.0 ? __longlong_as_double((long long)ONE_MINUS_ULP_BITS) : r;
 }
 
@@ -234,6 +234,56 @@ __device__ __forceinline__ double unit_int(u64 c, const InstParams &P)
         E++;
     }
     u64 bits = ((u64)(E + 1023) << 52) | (q1 & ((1ULL << 52) - 1));
+    if (bits > ONE_MINUS_ULP_BITS)
+        bits = ONE_MINUS_ULP_BITS;
+    return __longlong_as_double((long long)bits);
+}
+
+// The same value as unit_int, usually without the exact division. With X =
+// Mc 2^11 and D = Mn 2^11 (both in [2^63, 2^64)) and v the invariant
+// reciprocal of D, A = X + hi64(X v) approximates (X / D) 2^64 from below with
+// an error under 3 units (the low 32x32 partial product of X v is omitted).
+// The 53-bit significand is A's top bits; the bits below it decide the
+// rounding, and only when they lie within 3 units of the halfway point can
+// the error change the decision: then the exact routine decides. Rounding c
+// to 53 bits uses the add-half-minus-one-plus-lsb rule (ties to even) on the
+// left-normalised c; c < n < 2^64 - 2^35, so the addition cannot wrap.
+__device__ __forceinline__ double unit_int_fast(u64 c, const InstParams &P)
+{
+    if (c == 0)
+        return 0.0;
+    const int lz = __clzll(c);
+    const u64 t = c << lz;                                       // top bit set
+    const u64 tr = t + (0x3FFULL + ((t >> 11) & 1));             // round at bit 11
+    const bool carry = tr < t;                                   // rounded up to 2^64
+    const u64 X = carry ? (1ULL << 63) : (tr & ~0x7FFULL);       // Mc << 11
+    const int ec = 11 - lz + (carry ? 1 : 0);                    // RN(c) = (X >> 11) 2^ec
+    const u64 v = P.dv;
+    const u32 x0 = (u32)X, x1 = (u32)(X >> 32), v0 = (u32)v, v1 = (u32)(v >> 32);
+    const u64 a = (u64)x1 * v0, b = (u64)x0 * v1;
+    const u64 mid = a + b;
+    const u64 hi = (u64)x1 * v1 + (mid >> 32) + ((u64)(mid < a) << 32);  // <= hi64(X v)
+    const u64 A = X + hi;
+    const bool ge1 = A < X;  // X/D >= 1 (bit 64 of X + hi)
+    int E;
+    u64 q, g, half;
+    if (ge1) {  // significand = top 53 of the 65-bit A: bits 64..12
+        q = (A >> 12) | (1ULL << 52);
+        g = A & 0xFFF;
+        half = 0x800;
+        E = ec - P.en;
+    } else {  // bits 63..11
+        q = A >> 11;
+        g = A & 0x7FF;
+        half = 0x400;
+        E = ec - P.en - 1;
+    }
+    if (g + 3 >= half && g <= half)
+        return unit_int(c, P);  // the error could cross the halfway point
+    q += (g > half) ? 1 : 0;
+    // q in [2^52, 2^53]; adding q to the exponent field one below carries a
+    // rounded-up 2^53 into the exponent.
+    u64 bits = ((u64)(E + 1022) << 52) + q;
     if (bits > ONE_MINUS_ULP_BITS)
         bits = ONE_MINUS_ULP_BITS;
     return __longlong_as_double((long long)bits);

@@ -187,6 +187,7 @@ void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
         sh++;
     }
     o.en = sh;
+    o.dn = (double)n;  // round to nearest even
     o.dnorm = mn << 11;
     const u128 all = ~(u128)0;
     o.dv = (u64)(all / o.dnorm - ((u128)1 << 64));

@@ -44,7 +44,8 @@ struct alignas(16) InstParams {
     u32 a;           // skip multiplier
     u32 root;        // index into kRoots (power tables)
     int32_t en;      // RN(n) = Mn * 2^en, Mn in [2^52, 2^53)
-    u32 pad[3];
+    u32 pad;
+    double dn;       // RN(n) as a double
 };
 static_assert(sizeof(InstParams) == 96, "InstParams layout");
 

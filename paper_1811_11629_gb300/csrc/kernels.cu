@@ -84,13 +84,16 @@ __device__ __forceinline__ void encrypt(const u64 (&m)[L], u64 (&c)[L], const In
         dev::encrypt_mont64<L>(m, c, P);
 }
 
+// Division route for output j of a thread's run.
 template <int DIV>
-__device__ __forceinline__ double to_unit(u64 c, const InstParams &P)
+__device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
 {
     if constexpr (DIV == DIVIDE_INT)
-        return dev::unit_int(c, P);
+        return dev::unit_int_fast(c, P);
+    else if constexpr (DIV == DIVIDE_FP64)
+        return dev::unit_fp64(c, P.dn);
     else
-        return dev::unit_fp64(c, P.n);
+        return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_fp64(c, P.dn);
 }
 
 template <int L, int MODEXP, int DIV>
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
             for (int j = 0; j < L; j++) {
                 const int i = sidx(my0 + j);
                 if (out_r)
-                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P));
+                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
                 if (out_c)
                     st_c[i] = c[j];
             }
@@ -319,6 +322,12 @@ const void *select_kernel(int L, int modexp, int divide)
     RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_FP64)
     RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_FP64)
     RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_HYBRID)
 #undef RSAPRNG_SEL
     return nullptr;
 }
@@ -331,7 +340,7 @@ __global__ void k_unit(const InstParams *__restrict__ params, uint32_t id,
     const InstParams P = params[id];
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-        r[i] = to_unit<DIV>(c[i], P);
+        r[i] = to_unit<DIV>(c[i], P, 0);
 }
 
 // ---------------------------------------------------------------- microbenchmarks
@@ -354,6 +363,37 @@ __global__ void k_mb_imad(uint32_t iters, uint32_t seed, uint32_t *sink)
 #pragma unroll
     for (int j = 0; j < 8; j++)
         acc ^= x[j];
+    if (acc == 0x12345678u)
+        sink[0] = acc;
+}
+
+// Multiply-instruction shapes: 0 = widening 32x32->64 (IMAD.WIDE), 1 = high
+// half (IMAD.HI), 2 = one 32-bit Montgomery product (as in the chains).
+template <int S>
+__global__ void k_mb_mul(uint32_t iters, uint32_t k, uint32_t p, uint32_t pinv, uint32_t *sink)
+{
+    uint32_t x[8];
+    uint64_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        x[j] = (threadIdx.x * 8 + j + 1) % p;
+        w[j] = x[j];
+    }
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (S == 0)
+                w[j] = (uint64_t)(uint32_t)w[j] * k + (w[j] >> 32);
+            else if (S == 1)
+                x[j] = __umulhi(x[j], k) ^ (uint32_t)j;
+            else
+                x[j] = dev::mont32(x[j], x[j], p, pinv);
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        acc ^= x[j] ^ (uint32_t)w[j];
     if (acc == 0x12345678u)
         sink[0] = acc;
 }
@@ -437,6 +477,12 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
     RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_FP64)
     RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_FP64)
     RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_HYBRID)
 #undef RSAPRNG_DISPATCH
     return cudaErrorInvalidValue;
 }
@@ -483,7 +529,7 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
     if (N == 0)
         return cudaSuccess;
     const int grid = num_sms() * 8;
-    if (divide == DIVIDE_FP64)
+    if (divide == DIVIDE_FP64 || divide == DIVIDE_HYBRID)
         k_unit<DIVIDE_FP64><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     else
         k_unit<DIVIDE_INT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
@@ -501,6 +547,34 @@ cudaError_t microbench_imad(double *gops, cudaStream_t stream)
     const uint32_t iters = 1 << 16;
     float ms = 0;
     e = time_it([&] { k_mb_imad<<<grid, threads, 0, stream>>>(iters, 7u, sink); }, stream, &ms);
+    cudaFree(sink);
+    *gops = (double)grid * threads * iters * 8 / (ms * 1e-3) / 1e9;
+    return e;
+}
+
+cudaError_t microbench_mul(int shape, double *gops, cudaStream_t stream)
+{
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 64);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = num_sms();
+    const int grid = sms * 8, threads = 256;
+    const uint32_t iters = 1 << 12;
+    const uint32_t p = 4294967291u;  // the largest prime below 2^32
+    uint32_t pinv = p;
+    for (int i = 0; i < 4; i++)
+        pinv *= 2 - p * pinv;
+    float ms = 0;
+    if (shape == 0)
+        e = time_it([&] { k_mb_mul<0><<<grid, threads, 0, stream>>>(iters, 12345u, p, pinv, sink); },
+                    stream, &ms);
+    else if (shape == 1)
+        e = time_it([&] { k_mb_mul<1><<<grid, threads, 0, stream>>>(iters, 12345u, p, pinv, sink); },
+                    stream, &ms);
+    else
+        e = time_it([&] { k_mb_mul<2><<<grid, threads, 0, stream>>>(iters, 12345u, p, pinv, sink); },
+                    stream, &ms);
     cudaFree(sink);
     *gops = (double)grid * threads * iters * 8 / (ms * 1e-3) / 1e9;
     return e;

@@ -50,7 +50,9 @@ struct PrepGroup {
 };
 
 enum Modexp { MODEXP_CRT32 = 1, MODEXP_MONT64 = 2 };
-enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2 };
+// DIVIDE_HYBRID sends three of every four outputs of a thread through the
+// FP64 pipe and the fourth through the integer pipes (identical results).
+enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2, DIVIDE_HYBRID = 3 };
 
 struct DeviceTables {
     const InstParams *params;
@@ -87,6 +89,7 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
 // Microbenchmarks (results in the units documented in rsaprng.h).
 cudaError_t microbench_imad(double *gops, cudaStream_t stream);
 cudaError_t microbench_ddiv(double *gdiv, cudaStream_t stream);
+cudaError_t microbench_mul(int shape, double *gops, cudaStream_t stream);
 cudaError_t microbench_write(void *buf, size_t bytes, double *gbs, cudaStream_t stream);
 
 // Kernel attribute query for occupancy-based grid sizing.

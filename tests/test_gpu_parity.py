@@ -80,7 +80,8 @@ def test_plain_one_instance_1e6_full(O):
 
 
 ROUTES = [(R.MODEXP_CRT32, R.DIVIDE_INT), (R.MODEXP_CRT32, R.DIVIDE_FP64),
-          (R.MODEXP_MONT64, R.DIVIDE_INT), (R.MODEXP_MONT64, R.DIVIDE_FP64)]
+          (R.MODEXP_CRT32, R.DIVIDE_HYBRID), (R.MODEXP_MONT64, R.DIVIDE_INT),
+          (R.MODEXP_MONT64, R.DIVIDE_FP64), (R.MODEXP_MONT64, R.DIVIDE_HYBRID)]
 TILES = [(128, 2), (128, 8), (256, 4), (512, 2), (512, 8), (256, 8)]
 
 
