@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the plain / batched / served forms")
     ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
     ap.add_argument("--instances", type=int, default=0,
                     help="override the instance count (small profiling runs only)")
@@ -59,6 +61,10 @@ def parse_args(argv=None):
     ap.add_argument("--per-thread", type=int, default=0)
     ap.add_argument("--modexp", type=int, default=0)
     ap.add_argument("--divide", type=int, default=0)
+    ap.add_argument("--e-rule", default="", choices=["", "smallest", "uniform", "at_least"],
+                    help="override the exponent rule (experiments only)")
+    ap.add_argument("--e-lo", type=int, default=0)
+    ap.add_argument("--e-hi", type=int, default=0)
     return ap.parse_args(argv)
 
 
@@ -171,19 +177,20 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- roofline
-def mul_instr_per_number(e: int) -> int:
-    """32-bit integer multiply instructions the CRT route needs per output.
+def imad_slots_per_number(e: int) -> int:
+    """Integer-multiply pipe slots the CRT route needs per output (algorithmic count).
 
-    Per prime: REDC of m (2), then (bitlen(e)-1) squarings, (popcount(e)-1)
-    multiplies and one correction, each a Montgomery product of 3 multiplies
-    (widening a*b, low m*pinv, high mq*p). Garner: one Montgomery product (3)
-    and the widening h*q (1). Skip a*s mod Q: 2 widening + 1. Integer
-    division: the 64x64->128 reciprocal product (4 widening + 2) and the low
-    64-bit product q*d (3).
+    A slot is one 32-bit low multiply (IMAD) per lane; a high-half multiply
+    (IMAD.HI) or a widening 32x32->64 multiply (IMAD.WIDE) issues at half that
+    rate and counts 2. One 32-bit Montgomery product = widening a*b (2) + low
+    m*pinv (1) + high mq*p (2) = 5. Per output: 2 (bitlen(e) + popcount(e) - 1)
+    chain products (squarings, multiplies and the final correction, for p and
+    q) and the Garner product (1) = 5 (2k + 1) slots; REDC of m for p and q
+    (2 x (1 + 2)); the skip a*s mod Q (two widening products and 25*H: 5);
+    Garner's h*q (2); the integer division (three widening products: 6).
     """
-    b, w = e.bit_length(), bin(e).count("1")
-    per_prime = 2 + 3 * ((b - 1) + (w - 1) + 1)
-    return 2 * per_prime + 4 + 3 + 9
+    k = e.bit_length() + bin(e).count("1") - 1
+    return 5 * (2 * k + 1) + 6 + 5 + 2 + 6
 
 
 def load_peaks() -> dict:
@@ -228,6 +235,120 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
                       f"route=paper (Schrage + CRT), {dt:.1f} s wall"}
 
 
+# --------------------------------------------------------------------------- other forms
+def _slots(es, counts) -> float:
+    return float(sum(imad_slots_per_number(int(e)) * int(c) for e, c in zip(es, counts)))
+
+
+def form_plain(R, torch, device, peak_alu, rank) -> dict:
+    """Plain method: one instance, 1e6 outputs as uint64 c_k and float64 r_k per call."""
+    cfg = workload.CONFIGS["plain_1x1e6"]
+    ctx = R.Context(4, device=device)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], 1, first=rank),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    n = cfg["count"]
+    oc = torch.empty(n, dtype=torch.int64, device="cuda")
+    orr = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.generate_both(first, n, oc, orr)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    a.record()
+    for _ in range(reps):
+        ctx.generate_both(first, n, oc, orr)
+    b.record()
+    torch.cuda.synchronize()
+    dt = a.elapsed_time(b) / 1e3 / reps
+    e = ctx.params(first)[2]
+    out = {"value": round(n / dt / 1e9, 3), "unit": UNIT, "ms_per_call": round(dt * 1e3, 4),
+           "e": e, "outputs": "u64+f64",
+           "alu_frac": round(_slots([e], [n]) / dt / 1e9 / peak_alu, 4),
+           "hbm_GBps": round(16 * n / dt / 1e9, 1)}
+    ctx.close()
+    return out
+
+
+def form_batched(R, torch, device, peak_alu, rank) -> dict:
+    """Batched uneven: 1e5 instances, lognormal lengths (~2^32 outputs, f64), one plan in a
+    CUDA graph after autotuning on a 2000-instance sample."""
+    cfg = workload.CONFIGS["batched_1e5_lognormal"]
+    k = cfg["instances"]
+    lens = workload.lognormal_lengths(cfg["master"] + 1000 * rank, k)
+    ctx = R.Context(k, device=device)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    ids = np.arange(first, first + k, dtype=np.uint32)
+    tuned = ctx.autotune(ids[:2000], lens[:2000], reps=1)
+    plan = ctx.plan(ids, lens)
+    total = int(lens.sum())
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+    plan.capture(out_r=out, stream=st)
+    for _ in range(2):
+        plan.replay(stream=st)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(st)
+    for _ in range(reps):
+        plan.replay(stream=st)
+    b.record(st)
+    st.synchronize()
+    dt = a.elapsed_time(b) / 1e3 / reps
+    es = [ctx.params(int(i))[2] for i in ids]
+    res = {"value": round(total / dt / 1e9, 3), "unit": UNIT, "ms_per_replay": round(dt * 1e3, 3),
+           "numbers": total, "launches_per_replay": plan.info()["launches"],
+           "chunks": plan.info()["chunks"],
+           "alu_frac": round(_slots(es, lens) / dt / 1e9 / peak_alu, 4),
+           "tuned": {x: tuned[x] for x in ("modexp", "divide", "threads_per_block",
+                                           "numbers_per_thread")}}
+    plan.close()
+    del out
+    ctx.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dict:
+    """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
+    [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
+    cfg = workload.CONFIGS["serving_1e6"]
+    k = cfg["instances"]
+    ctx = R.Context(k, device=device)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
+    nreq = 4000
+    pick = first + workload.uniform_indices(61, nreq, k)
+    cnt = workload.loguniform_counts(62, nreq, lo=16, hi=1 << 24)
+    mean_cnt = float(cnt.mean())
+    # capacity: all requests at once (arrival 0), the server batching freely
+    srv.replay(pick, cnt, np.zeros(nreq), timeout_s=300)
+    st0 = srv.stats()
+    cap_numbers = st0["numbers_done"] / max(st0["wall_s"], 1e-9)
+    cap_rate = cap_numbers / mean_cnt
+    points = []
+    for f in loads:
+        rate = f * cap_rate
+        arr = workload.poisson_arrivals(63 + int(f * 100), nreq, rate)
+        srv.replay(pick, cnt, arr, timeout_s=300)
+        st = srv.stats()
+        points.append({"load": f, "offered_req_per_s": round(rate, 1),
+                       "throughput": round(st["numbers_done"] / st["wall_s"] / 1e9, 3),
+                       "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                       "iterations": st["iterations"]})
+    es = [ctx.params(int(i))[2] for i in pick[:200]]
+    mean_slots = float(np.mean([imad_slots_per_number(int(e)) for e in es]))
+    srv.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    mid = points[len(points) // 2]
+    return {"value": round(cap_numbers / 1e9, 3), "unit": UNIT,
+            "capacity_req_per_s": round(cap_rate, 1), "requests_per_point": nreq,
+            "mean_count": round(mean_cnt, 1), "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
+            "at_load": mid["load"], "alu_frac": round(cap_numbers * mean_slots / 1e9 / peak_alu, 4),
+            "points": points}
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(args) -> int:
     import torch
@@ -241,6 +362,11 @@ def run_ours(args) -> int:
         cfg["instances"] = args.instances
     if args.count:
         cfg["count"] = args.count
+    if args.e_rule:
+        cfg["e_rule"] = {"smallest": workload.E_SMALLEST, "uniform": workload.E_UNIFORM,
+                         "at_least": workload.E_AT_LEAST}[args.e_rule]
+        cfg["e_lo"] = args.e_lo or 3
+        cfg["e_hi"] = args.e_hi or cfg["e_lo"]
     k, n = cfg["instances"], cfg["count"]
     seeds = rank_seeds(cfg, dist.rank)
     knobs = {x: y for x, y in (("threads_per_block", args.threads),
@@ -290,10 +416,10 @@ def run_ours(args) -> int:
 
     # Roofline of the generation kernel (one launch per step, plus a 4-byte ticket reset).
     kern_s = statistics.mean(step_ms) / 1e3
-    ops = sum(mul_instr_per_number(int(e)) for e in es) * n
+    ops = sum(imad_slots_per_number(int(e)) for e in es) * n
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    peak_alu = 152 * 64 * sm_max * 1e6 / 1e9  # G multiply lane-ops/s: 152 SMs x 64 lanes/clk
+    peak_alu = 152 * 64 * sm_max * 1e6 / 1e9  # G IMAD slots/s: 152 SMs x 64 lanes/clk
     achieved = ops / kern_s / 1e9
     hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
     hbm_achieved = numbers_per_step * 8 / kern_s / 1e9
@@ -310,8 +436,9 @@ def run_ours(args) -> int:
                    "l2": "outputs 8 GiB per step > L2: no flush"},
         "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
                      "unit": "Gop/s", "frac": round(achieved / peak_alu, 4), "traffic": None,
-                     "op": "32-bit integer multiply instruction (IMAD/IMAD.HI/IMAD.WIDE) per lane",
-                     "ops_per_step": ops, "peak_source": "152 SMs x 64 IMAD lanes/clk x sm_max",
+                     "op": "integer-multiply pipe slot (IMAD = 1, IMAD.HI / IMAD.WIDE = 2) per lane",
+                     "ops_per_step": ops,
+                     "peak_source": "152 SMs x 64 IMAD lanes/clk x sm_max (nominal unit count)",
                      "kernel_ms": round(kern_s * 1e3, 3),
                      "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak,
                              "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4),
@@ -328,8 +455,10 @@ def run_ours(args) -> int:
     result["config"]["kernel"] = {x: cur[x] for x in ("modexp", "divide", "threads_per_block",
                                                       "numbers_per_thread")}
     result["config"]["kernel"].update(plan.shape())
-    if (k, n) != (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]):
-        result["config"]["workload"] = f"bulk_{k}x{n} (reduced size, not the benchmark workload)"
+    if (k, n) != (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]) \
+            or args.e_rule:
+        result["config"]["workload"] = f"bulk_{k}x{n} e={args.e_rule or 'uniform'} " \
+                                       "(experiment, not the benchmark workload)"
     del out
     torch.cuda.empty_cache()
 
@@ -347,6 +476,13 @@ def run_ours(args) -> int:
                          "h2d_bytes_per_step": k * 40 + 256,
                          "d2h_bytes_per_step": numbers_per_step * 8}
         del h_out
+    if not args.no_forms:
+        # The plain, batched and served forms of the same path on this GPU.
+        result["forms"] = {
+            "plain_1x1e6": form_plain(R, torch, dist.local_rank, peak_alu, dist.rank),
+            "batched_1e5_lognormal": form_batched(R, torch, dist.local_rank, peak_alu, dist.rank),
+            "serving_1e6": form_served(R, torch, dist.local_rank, peak_alu, dist.rank),
+        }
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)
     if dist.rank == 0:

@@ -85,8 +85,11 @@ enum {
     RSAPRNG_DIVIDE_INT = 1,   /* integer rounding + division by the invariant
                                  significand of RN(n) (Moller & Granlund 2011) */
     RSAPRNG_DIVIDE_FP64 = 2,  /* IEEE double conversion and division */
-    RSAPRNG_DIVIDE_HYBRID = 3 /* FP64 for three outputs in four, integer for the
-                                 fourth: keeps both the FP64 and integer pipes busy */
+    RSAPRNG_DIVIDE_HYBRID = 3,/* reciprocal route for three outputs in four, integer
+                                 for the fourth: keeps FP64 and integer pipes busy */
+    RSAPRNG_DIVIDE_RECIP = 4  /* FP64 multiply by the instance's correctly rounded
+                                 reciprocal of RN(n) and one fused multiply-add
+                                 correction (Markstein 1990); no division */
 };
 /* Exponent rules for rsaprng_params_from_seed. */
 enum { RSAPRNG_E_SMALLEST = 0, RSAPRNG_E_UNIFORM = 1, RSAPRNG_E_AT_LEAST = 2 };

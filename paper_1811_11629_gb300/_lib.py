@@ -22,7 +22,7 @@ pvp = ctypes.POINTER(ctypes.c_void_p)
 
 OK = 0
 MODEXP_AUTO, MODEXP_CRT32, MODEXP_MONT64 = 0, 1, 2
-DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID = 0, 1, 2, 3
+DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_RECIP = 0, 1, 2, 3, 4
 E_SMALLEST, E_UNIFORM, E_AT_LEAST = 0, 1, 2
 Q = (1 << 63) - 25
 DEFAULT_ROOT = 2307085864

@@ -44,7 +44,7 @@ static const rsaprng_config kDefaultConfig = {
 
 static int check_config(const rsaprng_config &c)
 {
-    if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 3)
+    if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 4)
         return fail(RSAPRNG_ERR_ARG, "config: modexp/divide out of range");
     if (c.threads_per_block && c.threads_per_block != 128 && c.threads_per_block != 256 &&
         c.threads_per_block != 512)
@@ -98,6 +98,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
     g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64     ? DIVIDE_FP64
                : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
+               : cfg.divide == RSAPRNG_DIVIDE_RECIP  ? DIVIDE_RECIP
                                                      : DIVIDE_INT;
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
     // Occupancy queries cost microseconds; cache them per kernel and smem size.
@@ -804,7 +805,9 @@ int rsaprng_unit_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, const uint64_t *
         divide = c->cfg.divide;
     cudaSetDevice(c->device);
     cudaError_t e = launch_unit(ctx_tables(c), id, N, d_c, d_r,
-                                divide == RSAPRNG_DIVIDE_INT ? DIVIDE_INT : DIVIDE_FP64,
+                                divide == RSAPRNG_DIVIDE_INT    ? DIVIDE_INT
+                                : divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64
+                                                                : DIVIDE_RECIP,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "unit launch");

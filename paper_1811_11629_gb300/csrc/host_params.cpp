@@ -189,6 +189,17 @@ void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
     o.en = sh;
     o.dn = (double)n;  // round to nearest even
     o.dnorm = mn << 11;
+    // RN(1/RN(n)) from integers: 1/Mn has significand 2^105/Mn in (2^52, 2^53]
+    // for Mn in [2^52, 2^53); round the exact quotient to nearest even.
+    {
+        const u128 num = (u128)1 << 105;
+        u64 qq = (u64)(num / mn);
+        const u64 rr = (u64)(num % mn);
+        if (2 * (u128)rr > mn || (2 * (u128)rr == mn && (qq & 1)))
+            qq++;
+        // 1/RN(n) = (qq / 2^105) 2^-en; qq <= 2^53 (qq = 2^53 only when Mn = 2^52)
+        o.recip = ldexp((double)qq, -105 - sh);
+    }
     const u128 all = ~(u128)0;
     o.dv = (u64)(all / o.dnorm - ((u128)1 << 64));
 }

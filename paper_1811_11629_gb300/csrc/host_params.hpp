@@ -46,8 +46,10 @@ struct alignas(16) InstParams {
     int32_t en;      // RN(n) = Mn * 2^en, Mn in [2^52, 2^53)
     u32 pad;
     double dn;       // RN(n) as a double
+    double recip;    // RN(1 / RN(n)), the correctly rounded reciprocal
+    u64 pad2;
 };
-static_assert(sizeof(InstParams) == 96, "InstParams layout");
+static_assert(sizeof(InstParams) == 112, "InstParams layout");
 
 // Validation codes mirror RSAPRNG_ERR_*.
 int validate_pqe(u64 p, u64 q, u64 e, bool require_safe);

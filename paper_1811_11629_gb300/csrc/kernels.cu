@@ -92,8 +92,10 @@ __device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
         return dev::unit_int_fast(c, P);
     else if constexpr (DIV == DIVIDE_FP64)
         return dev::unit_fp64(c, P.dn);
+    else if constexpr (DIV == DIVIDE_RECIP)
+        return dev::unit_recip(c, P.dn, P.recip);
     else
-        return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_fp64(c, P.dn);
+        return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_recip(c, P.dn, P.recip);
 }
 
 template <int L, int MODEXP, int DIV>
@@ -328,6 +330,12 @@ const void *select_kernel(int L, int modexp, int divide)
     RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_HYBRID)
     RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_HYBRID)
     RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_RECIP)
 #undef RSAPRNG_SEL
     return nullptr;
 }
@@ -483,6 +491,12 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
     RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_HYBRID)
     RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_HYBRID)
     RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_RECIP)
 #undef RSAPRNG_DISPATCH
     return cudaErrorInvalidValue;
 }
@@ -529,8 +543,10 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
     if (N == 0)
         return cudaSuccess;
     const int grid = num_sms() * 8;
-    if (divide == DIVIDE_FP64 || divide == DIVIDE_HYBRID)
+    if (divide == DIVIDE_FP64)
         k_unit<DIVIDE_FP64><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
+    else if (divide == DIVIDE_RECIP || divide == DIVIDE_HYBRID)
+        k_unit<DIVIDE_RECIP><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     else
         k_unit<DIVIDE_INT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     return cudaGetLastError();

@@ -51,8 +51,9 @@ struct PrepGroup {
 
 enum Modexp { MODEXP_CRT32 = 1, MODEXP_MONT64 = 2 };
 // DIVIDE_HYBRID sends three of every four outputs of a thread through the
-// FP64 pipe and the fourth through the integer pipes (identical results).
-enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2, DIVIDE_HYBRID = 3 };
+// FP64 pipe and the fourth through the integer pipes; DIVIDE_RECIP uses the
+// reciprocal-and-correction sequence on the FP64 pipe (identical results).
+enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2, DIVIDE_HYBRID = 3, DIVIDE_RECIP = 4 };
 
 struct DeviceTables {
     const InstParams *params;

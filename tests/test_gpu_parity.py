@@ -81,7 +81,8 @@ def test_plain_one_instance_1e6_full(O):
 
 ROUTES = [(R.MODEXP_CRT32, R.DIVIDE_INT), (R.MODEXP_CRT32, R.DIVIDE_FP64),
           (R.MODEXP_CRT32, R.DIVIDE_HYBRID), (R.MODEXP_MONT64, R.DIVIDE_INT),
-          (R.MODEXP_MONT64, R.DIVIDE_FP64), (R.MODEXP_MONT64, R.DIVIDE_HYBRID)]
+          (R.MODEXP_MONT64, R.DIVIDE_FP64), (R.MODEXP_MONT64, R.DIVIDE_HYBRID),
+          (R.MODEXP_CRT32, R.DIVIDE_RECIP), (R.MODEXP_MONT64, R.DIVIDE_RECIP)]
 TILES = [(128, 2), (128, 8), (256, 4), (512, 2), (512, 8), (256, 8)]
 
 
@@ -215,7 +216,7 @@ def test_cribs_and_one_guard(O):
         check_stream(O, (p, q, e), m0, 1, c.cpu().numpy(), r.cpu().numpy())
 
 
-@pytest.mark.parametrize("divide", [R.DIVIDE_INT, R.DIVIDE_FP64])
+@pytest.mark.parametrize("divide", [R.DIVIDE_INT, R.DIVIDE_FP64, R.DIVIDE_RECIP])
 def test_unit_step_random_and_edges(O, divide):
     """The output step alone on chosen ciphertexts: random, near n, below 2^53, ties."""
     ctx = R.Context(8)
