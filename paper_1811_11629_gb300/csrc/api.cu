@@ -39,7 +39,7 @@ int cuda_fail(cudaError_t e, const char *what)
 }
 
 static const rsaprng_config kDefaultConfig = {
-    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT, 256, 8, 0, 1ULL << 18, 0,
+    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_HYBRID, 128, 16, 0, 1ULL << 18, 0,
     {0, 0, 0, 0, 0, 0, 0}};
 
 static int check_config(const rsaprng_config &c)
@@ -50,8 +50,8 @@ static int check_config(const rsaprng_config &c)
         c.threads_per_block != 512)
         return fail(RSAPRNG_ERR_ARG, "config: threads_per_block must be 128, 256 or 512");
     if (c.numbers_per_thread && c.numbers_per_thread != 2 && c.numbers_per_thread != 4 &&
-        c.numbers_per_thread != 8)
-        return fail(RSAPRNG_ERR_ARG, "config: numbers_per_thread must be 2, 4 or 8");
+        c.numbers_per_thread != 8 && c.numbers_per_thread != 16)
+        return fail(RSAPRNG_ERR_ARG, "config: numbers_per_thread must be 2, 4, 8 or 16");
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32)
         return fail(RSAPRNG_ERR_ARG, "config: blocks_per_sm out of range");
     return RSAPRNG_OK;
@@ -96,6 +96,8 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.threads = cfg.threads_per_block;
     g.L = cfg.numbers_per_thread;
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
+    if (g.modexp == MODEXP_MONT64 && g.L == 16)
+        g.L = 8;  // the 64-bit route has no 16-output tiling (register budget)
     g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64     ? DIVIDE_FP64
                : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
                : cfg.divide == RSAPRNG_DIVIDE_RECIP  ? DIVIDE_RECIP
@@ -103,7 +105,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
     // Occupancy queries cost microseconds; cache them per kernel and smem size.
     const int ti = g.threads / 128 - 1 < 0 ? 0 : (g.threads / 128 - 1 > 3 ? 3 : g.threads / 128 - 1);
-    const int li = g.L == 2 ? 0 : (g.L == 4 ? 1 : 2);
+    const int li = g.L == 2 ? 0 : (g.L == 4 ? 1 : (g.L == 8 ? 2 : 3));
     int &cached = c->occ_cache[ti][li][g.modexp - 1][g.divide - 1];
     size_t &cached_smem = c->occ_smem[ti][li][g.modexp - 1][g.divide - 1];
     int occ;

@@ -61,8 +61,8 @@ struct rsaprng_ctx {
     rsaprng::ScratchSlot slots[rsaprng::kScratchSlots];
     int next_slot = 0;
     uint64_t launches = 0;
-    int occ_cache[4][3][2][4];  // blocks/SM by (threads/128-1, L index, modexp, divide)
-    size_t occ_smem[4][3][2][4];
+    int occ_cache[4][4][2][4];  // blocks/SM by (threads/128-1, L index, modexp, divide)
+    size_t occ_smem[4][4][2][4];
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
 };

@@ -315,6 +315,10 @@ const void *select_kernel(int L, int modexp, int divide)
     RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_SEL(16, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_SEL(16, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_SEL(16, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_SEL(16, MODEXP_CRT32, DIVIDE_RECIP)
     RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_FP64)
@@ -476,6 +480,10 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
     RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_DISPATCH(16, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_DISPATCH(16, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_DISPATCH(16, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_DISPATCH(16, MODEXP_CRT32, DIVIDE_RECIP)
     RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_FP64)

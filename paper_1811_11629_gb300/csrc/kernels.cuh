@@ -12,7 +12,7 @@ namespace rsaprng {
 // rows: pow_lin[root][i] = a^i mod Q for i in [0, kMaxTile], pow2k[root][b] =
 // a^(2^b) mod Q for b in [0, 63].
 constexpr int kMaxThreads = 1024;
-constexpr int kMaxL = 8;
+constexpr int kMaxL = 16;
 constexpr int kMaxTile = kMaxThreads * kMaxL;
 constexpr int kPowLinRow = kMaxTile + 1;
 

@@ -246,8 +246,15 @@ int rsaprng_generate_batch_host(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id 
         uint64_t *d_c = h_c ? (uint64_t *)(base + (h_r ? per * 8 : 0)) : nullptr;
         if (copy_pending[buf])
             cudaStreamWaitEvent(st, copy_done[buf], 0);
+        // Chunk the slice so that every SM has work even when it holds few requests.
+        const rsaprng_config saved = c->cfg;
+        const uint64_t tile = (uint64_t)c->cfg.threads_per_block * c->cfg.numbers_per_thread;
+        uint64_t chunk = per / ((uint64_t)c->sms * 8);
+        chunk = std::max<uint64_t>(tile, (chunk + tile - 1) / tile * tile);
+        c->cfg.chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(saved.chunk, tile));
         rc = rsaprng_generate_batch(c, parts.size(), sid.data(), scnt.data(), soff.data(), d_r, d_c,
                                     stream);
+        c->cfg = saved;
         if (rc)
             break;
         cudaEventRecord(gen_done[buf], st);
@@ -345,12 +352,15 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
     float best_ms = 1e30f;
     int rc = RSAPRNG_OK;
     // Stage 1: routes at the default tiling. Stage 2: tilings for the best route.
-    const int routes[4][2] = {{RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT},
-                              {RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_FP64},
+    const int routes[5][2] = {{RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_INT},
+                              {RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_HYBRID},
+                              {RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP},
                               {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_INT},
-                              {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_FP64}};
+                              {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_HYBRID}};
     for (auto &rt : routes) {
         rsaprng_config cfg = c->cfg;
+        if (rt[0] == RSAPRNG_MODEXP_MONT64 && cfg.numbers_per_thread == 16)
+            cfg.numbers_per_thread = 8;
         cfg.modexp = rt[0];
         cfg.divide = rt[1];
         float ms;
@@ -361,10 +371,13 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
             best = cfg;
         }
     }
-    const int tiles[][2] = {{128, 4}, {128, 8}, {256, 2}, {256, 4}, {256, 8}, {512, 2}, {512, 4}};
+    const int tiles[][2] = {{128, 4},  {128, 8}, {128, 16}, {256, 4}, {256, 8},
+                            {256, 16}, {512, 2}, {512, 4},  {512, 8}};
     for (auto &tl : tiles) {
         if (rc)
             break;
+        if (tl[1] == 16 && best.modexp == RSAPRNG_MODEXP_MONT64)
+            continue;
         rsaprng_config cfg = best;
         cfg.threads_per_block = tl[0];
         cfg.numbers_per_thread = tl[1];

@@ -83,7 +83,7 @@ ROUTES = [(R.MODEXP_CRT32, R.DIVIDE_INT), (R.MODEXP_CRT32, R.DIVIDE_FP64),
           (R.MODEXP_CRT32, R.DIVIDE_HYBRID), (R.MODEXP_MONT64, R.DIVIDE_INT),
           (R.MODEXP_MONT64, R.DIVIDE_FP64), (R.MODEXP_MONT64, R.DIVIDE_HYBRID),
           (R.MODEXP_CRT32, R.DIVIDE_RECIP), (R.MODEXP_MONT64, R.DIVIDE_RECIP)]
-TILES = [(128, 2), (128, 8), (256, 4), (512, 2), (512, 8), (256, 8)]
+TILES = [(128, 2), (128, 8), (256, 4), (512, 2), (512, 8), (256, 8), (128, 16), (256, 16)]
 
 
 @pytest.mark.parametrize("modexp,divide", ROUTES)
