@@ -193,6 +193,34 @@ def imad_slots_per_number(e: int) -> int:
     return 5 * (2 * k + 1) + 6 + 5 + 2 + 6
 
 
+KERNEL_SOURCES = ["paper_1811_11629_gb300/csrc/kernels.cu",
+                  "paper_1811_11629_gb300/csrc/device_math.cuh",
+                  "paper_1811_11629_gb300/csrc/kernels.cuh"]
+TRAFFIC_PROFILE = "profiles/dram_traffic_bulk_1024x2p20.md"
+
+
+def measured_traffic(kernel: dict):
+    """DRAM bytes per generation launch from the committed ncu capture, or None when the
+    kernel sources or its configuration changed since the capture."""
+    import hashlib
+
+    try:
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines()
+                  if line.startswith(("traffic_bytes_per_launch:", "kernel_sources_sha256:")))
+    if fields.get("kernel_sources_sha256", "").strip() != h.hexdigest():
+        return None
+    if (kernel.get("modexp"), kernel.get("divide"), kernel.get("threads_per_block"),
+            kernel.get("numbers_per_thread")) != (1, 3, 128, 16):
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def load_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -455,6 +483,8 @@ def run_ours(args) -> int:
     result["config"]["kernel"] = {x: cur[x] for x in ("modexp", "divide", "threads_per_block",
                                                       "numbers_per_thread")}
     result["config"]["kernel"].update(plan.shape())
+    if (k, n) == (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]):
+        result["roofline"]["traffic"] = measured_traffic(result["config"]["kernel"])
     if (k, n) != (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]) \
             or args.e_rule:
         result["config"]["workload"] = f"bulk_{k}x{n} e={args.e_rule or 'uniform'} " \
@@ -468,13 +498,16 @@ def run_ours(args) -> int:
         h_out = torch.empty(k * n, dtype=torch.float64, pin_memory=True)
         ctx.generate_batch_host(ids, counts, h_r=h_out)
         dist.barrier()
+        x0 = ctx.transfer_bytes()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.generate_batch_host(ids, counts, h_r=h_out)
         dt = dist.max(time.perf_counter() - t0)
+        x1 = ctx.transfer_bytes()
         result["e2e"] = {"value": round(total_numbers / dt / 1e9, 4), "unit": UNIT,
-                         "h2d_bytes_per_step": k * 40 + 256,
-                         "d2h_bytes_per_step": numbers_per_step * 8}
+                         "h2d_bytes_per_step": (x1[0] - x0[0]) // args.steps,
+                         "d2h_bytes_per_step": (x1[1] - x0[1]) // args.steps,
+                         "api": "rsaprng_generate_batch_host (pinned host output)"}
         del h_out
     if not args.no_forms:
         # The plain, batched and served forms of the same path on this GPU.

@@ -320,6 +320,9 @@ int rsaprng_unit_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, const uint64_t
 
 /* Kernel launches issued by this context so far (for launch accounting). */
 uint64_t rsaprng_launch_count(const rsaprng_ctx *ctx);
+/* Bytes the library itself has copied host->device (work lists) and
+ * device->host (rsaprng_generate_batch_host results) on this context. */
+int rsaprng_transfer_bytes(const rsaprng_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 
 /* ----------------------------------------------------- microbenchmarks */
 

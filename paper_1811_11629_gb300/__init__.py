@@ -121,6 +121,13 @@ class Context:
     def launches(self) -> int:
         return self.L.rsaprng_launch_count(self.h)
 
+    def transfer_bytes(self):
+        """(host->device, device->host) bytes the library has copied so far."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        check(self.L.rsaprng_transfer_bytes(self.h, ctypes.byref(a), ctypes.byref(b)),
+              "transfer_bytes")
+        return a.value, b.value
+
     # -- instances
     def create(self, p: int, q: int, e: int, seed: int) -> int:
         out = ctypes.c_uint32()

@@ -95,6 +95,7 @@ SIGNATURES = {
     "rsaprng_validate_params": (i32, [u64, u64, u64, i32]),
     "rsaprng_params_from_seed": (i32, [u64, i32, u64, u64, pu64, pu64, pu64, pu64]),
     "rsaprng_launch_count": (u64, [vp]),
+    "rsaprng_transfer_bytes": (i32, [vp, pu64, pu64]),
     "rsaprng_microbench": (i32, [vp, i32, u64, pdbl]),
     "rsaprng_unit_f64": (i32, [vp, u32, u64, vp, vp, i32, vp]),
     "rsaprng_strerror": (ctypes.c_char_p, [i32]),

@@ -299,6 +299,7 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     cudaError_t e = cudaMemcpyAsync(dp.d_buf, dp.h_buf, o, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "plan upload");
+    c->h2d_bytes += o;
     return RSAPRNG_OK;
 }
 
@@ -549,6 +550,17 @@ int rsaprng_ctx_get_config(const rsaprng_ctx *c, rsaprng_config *out)
 uint64_t rsaprng_instance_count(const rsaprng_ctx *c) { return c ? c->count : 0; }
 
 uint64_t rsaprng_launch_count(const rsaprng_ctx *c) { return c ? c->launches : 0; }
+
+int rsaprng_transfer_bytes(const rsaprng_ctx *c, uint64_t *h2d, uint64_t *d2h)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null");
+    if (h2d)
+        *h2d = c->h2d_bytes;
+    if (d2h)
+        *d2h = c->d2h_bytes;
+    return RSAPRNG_OK;
+}
 
 // Appends validated instances [count .. count+k) and writes them to the device.
 static int append_instances(rsaprng_ctx *c, const std::vector<InstParams> &ps,

@@ -278,6 +278,7 @@ int rsaprng_generate_batch_host(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id 
                 rc = cuda_fail(e, "result copy");
                 break;
             }
+            c->d2h_bytes += n * width;
             i = j;
         }
         cudaEventRecord(copy_done[buf], cp);
