@@ -76,9 +76,12 @@ class Dist:
         self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
         if self.world > 1:
+            import torch
             import torch.distributed as dist
 
             os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            if backend_gpu:
+                torch.cuda.set_device(self.local_rank)  # before NCCL binds a device
             dist.init_process_group("nccl" if backend_gpu else "gloo")
             self.pg = dist
 
@@ -344,10 +347,12 @@ def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dic
     ctx = R.Context(k, device=device)
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
                               cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
-    srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
     nreq = 4000
     pick = first + workload.uniform_indices(61, nreq, k)
     cnt = workload.loguniform_counts(62, nreq, lo=16, hi=1 << 24)
+    # tune the tiling on a sample of the request mix (the instance states are restored)
+    tuned = ctx.autotune(pick[:512], np.minimum(cnt[:512], 1 << 20), reps=1)
+    srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
     mean_cnt = float(cnt.mean())
     # capacity: all requests at once (arrival 0), the server batching freely
     srv.replay(pick, cnt, np.zeros(nreq), timeout_s=300)
@@ -374,6 +379,8 @@ def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dic
             "capacity_req_per_s": round(cap_rate, 1), "requests_per_point": nreq,
             "mean_count": round(mean_cnt, 1), "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
             "at_load": mid["load"], "alu_frac": round(cap_numbers * mean_slots / 1e9 / peak_alu, 4),
+            "tuned": {x: tuned[x] for x in ("modexp", "divide", "threads_per_block",
+                                            "numbers_per_thread")},
             "points": points}
 
 

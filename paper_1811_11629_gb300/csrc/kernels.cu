@@ -263,23 +263,40 @@ __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
 }
 
 // Start states of the chunks of each instance: m before chunk j is the
-// instance's m plus the skip sums of chunks 0..j-1 (mod n).
-__global__ void k_prep_scan(DeviceTables tab, const PrepGroup *__restrict__ groups, uint32_t ngroups,
-                            const PrepChunk *__restrict__ chunks, const u64 *__restrict__ chunk_sum,
-                            const u64 *__restrict__ chunk_s, WorkItem *__restrict__ items)
+// instance's m plus the skip sums of chunks 0..j-1 (mod n). One block per
+// group (grid-stride): each thread takes a contiguous run of chunks, the
+// block scans the run totals, and the threads write their chunks' states.
+constexpr int kScanT = 128;
+__global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
+                                                      const PrepGroup *__restrict__ groups,
+                                                      uint32_t ngroups,
+                                                      const PrepChunk *__restrict__ chunks,
+                                                      const u64 *__restrict__ chunk_sum,
+                                                      const u64 *__restrict__ chunk_s,
+                                                      WorkItem *__restrict__ items)
 {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ngroups)
-        return;
-    const PrepGroup G = groups[g];
-    const u64 n = tab.params[G.inst].n;
-    u64 m = tab.state_m[G.inst];
-    for (uint32_t j = 0; j < G.count; j++) {
-        const uint32_t k = G.first + j;
-        WorkItem &w = items[chunks[k].item];
-        w.m0 = m;
-        w.s0 = chunk_s[k];
-        m = addmod(m, chunk_sum[k], n);
+    __shared__ u64 sh_scan[32];
+    const int t = threadIdx.x;
+    for (uint32_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const PrepGroup G = groups[g];
+        const u64 n = tab.params[G.inst].n;
+        const u64 m0 = tab.state_m[G.inst];
+        const uint32_t per = (G.count + kScanT - 1) / kScanT;
+        const uint32_t j0 = min((uint32_t)t * per, G.count);
+        const uint32_t j1 = min(j0 + per, G.count);
+        u64 run = 0;
+        for (uint32_t j = j0; j < j1; j++)
+            run = addmod(run, chunk_sum[G.first + j], n);
+        u64 total;
+        u64 m = addmod(m0, block_exscan_mod(run, n, sh_scan, total), n);
+        for (uint32_t j = j0; j < j1; j++) {
+            const uint32_t k = G.first + j;
+            WorkItem &w = items[chunks[k].item];
+            w.m0 = m;
+            w.s0 = chunk_s[k];
+            m = addmod(m, chunk_sum[k], n);
+        }
+        __syncthreads();  // sh_scan is reused by the next group
     }
 }
 
@@ -538,10 +555,9 @@ cudaError_t launch_prep_scan(const DeviceTables &t, const PrepGroup *groups, uin
 {
     if (ngroups == 0)
         return cudaSuccess;
-    const int threads = 128;
-    const int grid = (int)((ngroups + threads - 1) / threads);
-    k_prep_scan<<<grid, threads, 0, stream>>>(t, groups, ngroups, chunks, chunk_sum, chunk_s,
-                                              items);
+    const int grid = (int)(ngroups < 65535u ? ngroups : 65535u);
+    k_prep_scan<<<grid, kScanT, 0, stream>>>(t, groups, ngroups, chunks, chunk_sum, chunk_s,
+                                             items);
     return cudaGetLastError();
 }
 

@@ -132,7 +132,10 @@ struct rsaprng_server {
     std::vector<uint64_t> busy;   // per instance: in-flight iteration (0 = free)
     std::vector<uint64_t> stamp;  // per instance: iteration that blocked it
     uint64_t next_ticket = 1, iter_counter = 0;
-    uint64_t per_req_cap = 1ULL << 24, per_iter_cap = 1ULL << 26;
+    // An iteration carries at most per_iter_cap numbers and at most
+    // per_req_cap of one request, so small requests are not queued behind a
+    // large one for long.
+    uint64_t per_req_cap = 1ULL << 22, per_iter_cap = 1ULL << 24;
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, cancelled = 0;
     uint64_t numbers_done = 0, iterations = 0;
@@ -275,10 +278,18 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
             return false;
         }
     }
-    // Outside the lock: plan, upload, launch.
+    // Outside the lock: plan, upload, launch. Chunks are sized so that the
+    // iteration spreads over all SMs.
+    uint64_t numbers = 0;
+    for (uint64_t x : counts)
+        numbers += x;
+    const uint64_t tile =
+        (uint64_t)S->ctx->cfg.threads_per_block * S->ctx->cfg.numbers_per_thread;
+    uint64_t chunk = numbers / ((uint64_t)S->ctx->sms * 8);
+    chunk = std::max<uint64_t>(tile, (chunk + tile - 1) / tile * tile);
+    chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(S->ctx->cfg.chunk, tile));
     HostPlan hp;
-    int rc = build_plan(S->ctx, ids.size(), ids.data(), counts.data(), offs.data(),
-                        S->ctx->cfg.chunk, hp);
+    int rc = build_plan(S->ctx, ids.size(), ids.data(), counts.data(), offs.data(), chunk, hp);
     if (rc == RSAPRNG_OK)
         rc = upload_plan(S->ctx, hp, sl.plan, sl.stream);
     if (rc == RSAPRNG_OK)
