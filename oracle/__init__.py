@@ -46,49 +46,57 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def load_library(path: str):
+    """A ctypes handle with the oracle's signatures for the library at `path`."""
+    L = ctypes.CDLL(path)
+    _configure(L)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            u64, i32, dbl = ctypes.c_uint64, ctypes.c_int, ctypes.c_double
-            pu64 = ctypes.POINTER(ctypes.c_uint64)
-            pdbl = ctypes.POINTER(ctypes.c_double)
-            sig = {
-                "or_q_default": (u64, []),
-                "or_mulmod": (u64, [u64, u64, u64]),
-                "or_addmod": (u64, [u64, u64, u64]),
-                "or_powmod": (u64, [u64, u64, u64]),
-                "or_gcd": (u64, [u64, u64]),
-                "or_invmod": (u64, [u64, u64]),
-                "or_is_prime": (i32, [u64]),
-                "or_count_primes": (None, [u64, u64, pu64, pu64]),
-                "or_skip_next_direct": (u64, [u64, u64, u64]),
-                "or_skip_next_schrage": (u64, [u64, u64, u64]),
-                "or_skip_jump": (u64, [u64, u64, u64, u64]),
-                "or_split_s0": (u64, [u64, u64, u64, u64, u64]),
-                "or_encrypt_direct": (u64, [u64, u64, u64]),
-                "or_crt_encrypt": (u64, [u64, u64, u64, u64, u64, u64]),
-                "or_unit": (dbl, [u64, u64]),
-                "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
-                "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
-                "or_sample": (i32, [ctypes.c_void_p, pu64, pu64, pu64, u64, pu64, pdbl]),
-                "or_sample_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64,
-                                         pu64, pu64, pu64, pdbl]),
-                "or_unit_many": (None, [pu64, u64, pdbl, u64]),
-                "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
-                                           pu64, pu64, pu64, pdbl, i32]),
-                "or_max_threads": (i32, []),
-                "or_splitmix64_next": (u64, [pu64]),
-                "or_params_from_seed": (i32, [u64, i32, u64, u64, pu64, pu64, pu64, pu64]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = load_library(build())
     return _lib
+
+
+def _configure(L):
+    u64, i32, dbl = ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    pu64 = ctypes.POINTER(ctypes.c_uint64)
+    pdbl = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "or_q_default": (u64, []),
+        "or_mulmod": (u64, [u64, u64, u64]),
+        "or_addmod": (u64, [u64, u64, u64]),
+        "or_powmod": (u64, [u64, u64, u64]),
+        "or_gcd": (u64, [u64, u64]),
+        "or_invmod": (u64, [u64, u64]),
+        "or_is_prime": (i32, [u64]),
+        "or_count_primes": (None, [u64, u64, pu64, pu64]),
+        "or_skip_next_direct": (u64, [u64, u64, u64]),
+        "or_skip_next_schrage": (u64, [u64, u64, u64]),
+        "or_skip_jump": (u64, [u64, u64, u64, u64]),
+        "or_split_s0": (u64, [u64, u64, u64, u64, u64]),
+        "or_encrypt_direct": (u64, [u64, u64, u64]),
+        "or_crt_encrypt": (u64, [u64, u64, u64, u64, u64, u64]),
+        "or_unit": (dbl, [u64, u64]),
+        "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
+        "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
+        "or_sample": (i32, [ctypes.c_void_p, pu64, pu64, pu64, u64, pu64, pdbl]),
+        "or_sample_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64,
+                                 pu64, pu64, pu64, pdbl]),
+        "or_unit_many": (None, [pu64, u64, pdbl, u64]),
+        "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
+                                   pu64, pu64, pu64, pdbl, i32]),
+        "or_max_threads": (i32, []),
+        "or_splitmix64_next": (u64, [pu64]),
+        "or_params_from_seed": (i32, [u64, i32, u64, u64, pu64, pu64, pu64, pu64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
 
 
 def _p64(a: np.ndarray):

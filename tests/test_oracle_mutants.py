@@ -1,0 +1,189 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (on the CPU),
+builds it, and runs the pin checks against that copy: at least one check
+must fail. The checks restate the pins of test_oracle_pins.py against raw C
+entry points so they can run on any build of the oracle.
+"""
+import ctypes
+import math
+import os
+import random
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "rsaprng_oracle.c")
+Q = (1 << 63) - 25
+A = 2307085864
+
+
+class P(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint64), ("q", ctypes.c_uint64), ("e", ctypes.c_uint64),
+                ("a", ctypes.c_uint64), ("Q", ctypes.c_uint64)]
+
+
+def _gen(L, p, q, e, m0, s0, n, a=A, qm=Q, route=0):
+    prm = P(p, q, e, a, qm)
+    m, s = ctypes.c_uint64(m0), ctypes.c_uint64(s0)
+    c = np.empty(n, np.uint64)
+    r = np.empty(n, np.float64)
+    rc = L.or_generate(ctypes.byref(prm), ctypes.byref(m), ctypes.byref(s), n,
+                       c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                       r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), route)
+    return rc, c, r, m.value, s.value
+
+
+def _sieve(lo, hi):
+    seg = np.ones(hi - lo, bool)
+    for d in range(2, int(math.isqrt(hi)) + 1):
+        start = max(d * d, (lo + d - 1) // d * d)
+        seg[start - lo::d] = False
+    return set((lo + np.nonzero(seg)[0]).tolist())
+
+
+PRIMES_WIN = None
+
+
+def check_primality(L):
+    global PRIMES_WIN
+    lo = 1 << 31
+    if PRIMES_WIN is None:
+        PRIMES_WIN = _sieve(lo, lo + (1 << 14))
+    if any(L.or_is_prime(x) for x in (2047, 1373653, 25326001, 3215031751, 2152302898747,
+                                       3474749660383, 341550071728321, 3825123056546413051)):
+        return False
+    if not L.or_is_prime(Q):
+        return False
+    return all(bool(L.or_is_prime(x)) == (x in PRIMES_WIN) for x in range(lo + 1, lo + (1 << 14), 2))
+
+
+def check_roots(L):
+    fs = [2, 3, 17, 23, 319279, 456065899]
+    prim = [g for g in range(2, 12)
+            if L.or_powmod(g, Q - 1, Q) == 1 and all(L.or_powmod(g, (Q - 1) // f, Q) != 1 for f in fs)]
+    return prim == [3, 6, 7, 10, 11]
+
+
+def check_skips(L):
+    rng = random.Random(1)
+    for a in (A, 3157107955, 3, 11):
+        for _ in range(300):
+            s = rng.randrange(1, Q)
+            if L.or_skip_next_schrage(s, a, Q) != a * s % Q or L.or_skip_next_direct(s, a, Q) != a * s % Q:
+                return False
+    return True
+
+
+def check_period_tiny_q(L):
+    qp, a, p, q = 47, 5, 5, 11
+    n, per = p * q, 46 * 55
+    rc, c, _, _, _ = _gen(L, p, q, 1, 7, 1, 2 * per, a=a, qm=qp)
+    if rc != 0:
+        return False
+    msgs = [int(x) for x in c]
+    b = qp * (qp - 1) // 2
+    counts = np.bincount(np.array(msgs[:per]), minlength=n)
+    return (counts == qp - 1).all() and all(msgs[k + qp - 1] == (msgs[k] + b) % n for k in range(per))
+
+
+def check_closed_form(L):
+    p, q, e = 2147483659, 2147483693, 5
+    n = p * q
+    rc, c, r, m_end, s_end = _gen(L, p, q, e, 12345, 1, 200)
+    if rc != 0:
+        return False
+    acc = 12345
+    for k in range(1, 201):
+        acc = (acc + pow(A, k, Q)) % n
+        if int(c[k - 1]) != pow(acc, e, n):
+            return False
+    return m_end == acc and s_end == pow(A, 200, Q)
+
+
+def check_rsa(L):
+    rng = random.Random(2)
+    p, q = 4294967291, 4294967279
+    n = p * q
+    qinv = pow(q, -1, p)
+    for e in (5, 7, 65537):
+        if math.gcd(e, (p - 1) * (q - 1)) != 1:
+            continue
+        d = pow(e, -1, (p - 1) * (q - 1))
+        for m in [0, 1, n - 1] + [rng.randrange(n) for _ in range(100)]:
+            c = L.or_encrypt_direct(m, e, n)
+            if c != pow(m, e, n) or pow(c, d, n) != m:
+                return False
+            if L.or_crt_encrypt(m % p, m % q, p, q, e, qinv) != c:
+                return False
+            if L.or_crt_encrypt(m % q, m % p, q, p, e, pow(p, -1, q)) != c:
+                return False
+    return True
+
+
+def check_unit(L):
+    rng = random.Random(3)
+    for n in (4294967291 * 4294967279, 2147483659 * 2147483693):
+        for c in [0, 1, n - 1, n - 2] + [rng.randrange(n) for _ in range(2000)]:
+            want = float(Fraction(float(c)) / Fraction(float(n)))
+            want = 0.9999999999999999 if want >= 1.0 else want
+            if L.or_unit(c, n) != want:
+                return False
+    return True
+
+
+def check_split(L):
+    return all(L.or_split_s0(1, A, Q, mv, g) == pow(A, g * ((Q - 1) // mv), Q)
+               for mv in (2, 32, 1000) for g in (0, 1, mv - 1))
+
+
+CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
+          check_rsa, check_unit, check_split]
+
+MUTANTS = {
+    "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
+                                "return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2) - 1);"),
+    "skip_wrong_modulus": ("return or_mulmod(a, s, Q);", "return or_mulmod(a, s, Q - 2);"),
+    "message_before_skip": ("            s = s_direct;\n            m = or_addmod(m, s % n, n);\n            mp = (mp + s) % p;\n            mq = (mq + s) % q;",
+                            "            m = or_addmod(m, s % n, n);\n            mp = (mp + s) % p;\n            mq = (mq + s) % q;\n            s = s_direct;"),
+    "garner_no_reduction": ("uint64_t diff = (cp + p - (cq % p)) % p;",
+                            "uint64_t diff = (cp + p - cq) % p;"),
+    "guard_strict": ("if (r >= 1.0)\n        r = 0x1.fffffffffffffp-1;",
+                     "if (r > 1.0)\n        r = 0x1.fffffffffffffp-1;"),
+    "four_mr_bases": ("int bases = (n < ((uint64_t)1 << 32)) ? 5 : 12;",
+                      "int bases = (n < ((uint64_t)1 << 32)) ? 4 : 12;"),
+    "no_square": ("        b = or_mulmod(b, b, m);\n        e >>= 1;\n    }\n    return r;\n}\n\n/* b^e mod m for m < 2^32",
+                  "        e >>= 1;\n    }\n    return r;\n}\n\n/* b^e mod m for m < 2^32"),
+    "split_off_by_one": ("u128 k = (u128)gamma * (u128)((Q - 1) / Mv);",
+                         "u128 k = (u128)(gamma + 1) * (u128)((Q - 1) / Mv);"),
+    "division_by_reciprocal": ("double r = dc / dn;", "double r = dc * (1.0 / dn);"),
+}
+
+
+@pytest.fixture(scope="module")
+def clean():
+    return oracle.lib()
+
+
+def test_pins_pass_on_the_oracle(clean):
+    for chk in CHECKS:
+        assert chk(clean), chk.__name__
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    before, after = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, name
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(before, after))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-o", str(so), str(mutated)], check=True)
+    L = oracle.load_library(str(so))
+    failed = [chk.__name__ for chk in CHECKS if not chk(L)]
+    assert failed, f"no pin catches the planted mistake {name}"
