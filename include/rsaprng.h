@@ -99,7 +99,7 @@ typedef struct {
     uint32_t struct_size;       /* sizeof(rsaprng_config) */
     int32_t modexp;             /* RSAPRNG_MODEXP_* */
     int32_t divide;             /* RSAPRNG_DIVIDE_* */
-    int32_t threads_per_block;  /* 128, 256, 512 or 1024 */
+    int32_t threads_per_block;  /* 64, 128, 256 or 512 */
     int32_t numbers_per_thread; /* 2, 4, 8 or 16 (the 64-bit route uses 8 for 16) */
     int32_t blocks_per_sm;      /* persistent-launch occupancy target */
     uint64_t chunk;             /* numbers per chunk of a long stream (multiple

@@ -46,9 +46,9 @@ static int check_config(const rsaprng_config &c)
 {
     if (c.modexp < 0 || c.modexp > 2 || c.divide < 0 || c.divide > 4)
         return fail(RSAPRNG_ERR_ARG, "config: modexp/divide out of range");
-    if (c.threads_per_block && c.threads_per_block != 128 && c.threads_per_block != 256 &&
-        c.threads_per_block != 512)
-        return fail(RSAPRNG_ERR_ARG, "config: threads_per_block must be 128, 256 or 512");
+    if (c.threads_per_block && c.threads_per_block != 64 && c.threads_per_block != 128 &&
+        c.threads_per_block != 256 && c.threads_per_block != 512)
+        return fail(RSAPRNG_ERR_ARG, "config: threads_per_block must be 64, 128, 256 or 512");
     if (c.numbers_per_thread && c.numbers_per_thread != 2 && c.numbers_per_thread != 4 &&
         c.numbers_per_thread != 8 && c.numbers_per_thread != 16)
         return fail(RSAPRNG_ERR_ARG, "config: numbers_per_thread must be 2, 4, 8 or 16");
@@ -96,7 +96,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.threads = cfg.threads_per_block;
     g.L = cfg.numbers_per_thread;
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
-    if (g.modexp == MODEXP_MONT64 && g.L == 16)
+    if (g.modexp == MODEXP_MONT64 && g.L > 8)
         g.L = 8;  // the 64-bit route has no 16-output tiling (register budget)
     g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64     ? DIVIDE_FP64
                : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
@@ -104,7 +104,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
                                                      : DIVIDE_INT;
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
     // Occupancy queries cost microseconds; cache them per kernel and smem size.
-    const int ti = g.threads / 128 - 1 < 0 ? 0 : (g.threads / 128 - 1 > 3 ? 3 : g.threads / 128 - 1);
+    const int ti = g.threads == 64 ? 0 : (g.threads == 128 ? 1 : (g.threads == 256 ? 2 : 3));
     const int li = g.L == 2 ? 0 : (g.L == 4 ? 1 : (g.L == 8 ? 2 : 3));
     int &cached = c->occ_cache[ti][li][g.modexp - 1][g.divide - 1];
     size_t &cached_smem = c->occ_smem[ti][li][g.modexp - 1][g.divide - 1];

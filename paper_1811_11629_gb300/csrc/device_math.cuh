@@ -104,16 +104,27 @@ __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], cons
     }
     const int top = 31 - __clz(e);
     for (int bit = top - 1; bit >= 0; bit--) {
+        u64 Tp[L], Tq[L];
 #pragma unroll
         for (int j = 0; j < L; j++) {
-            zp[j] = mont32(zp[j], zp[j], p, pinv);
-            zq[j] = mont32(zq[j], zq[j], q, qinv);
+            Tp[j] = (u64)zp[j] * zp[j];
+            Tq[j] = (u64)zq[j] * zq[j];
+        }
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            zp[j] = redc32(Tp[j], p, pinv);
+            zq[j] = redc32(Tq[j], q, qinv);
         }
         if ((e >> bit) & 1) {
 #pragma unroll
             for (int j = 0; j < L; j++) {
-                zp[j] = mont32(zp[j], yp[j], p, pinv);
-                zq[j] = mont32(zq[j], yq[j], q, qinv);
+                Tp[j] = (u64)zp[j] * yp[j];
+                Tq[j] = (u64)zq[j] * yq[j];
+            }
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                zp[j] = redc32(Tp[j], p, pinv);
+                zq[j] = redc32(Tq[j], q, qinv);
             }
         }
     }
