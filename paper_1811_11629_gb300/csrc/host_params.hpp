@@ -28,7 +28,7 @@ bool is_prime(u64 x);      // Sec. V: trial division + deterministic Rabin-Mille
 // SplitMix64 step (Steele, Lea & Flood 2014).
 u64 splitmix64_next(u64 &state);
 
-// Device-side record of one instance's fixed parameters (96 bytes). Field
+// Device-side record of one instance's fixed parameters (112 bytes). Field
 // meaning is documented at the kernels that read it.
 struct alignas(16) InstParams {
     u64 n;       // p q
