@@ -219,7 +219,7 @@ def measured_traffic(kernel: dict):
     if fields.get("kernel_sources_sha256", "").strip() != h.hexdigest():
         return None
     if (kernel.get("modexp"), kernel.get("divide"), kernel.get("threads_per_block"),
-            kernel.get("numbers_per_thread")) != (1, 3, 128, 16):
+            kernel.get("numbers_per_thread")) != (1, 4, 128, 16):
         return None
     return int(fields["traffic_bytes_per_launch"])
 

@@ -102,8 +102,11 @@ typedef struct {
     int32_t threads_per_block;  /* 64, 128, 256 or 512 */
     int32_t numbers_per_thread; /* 2, 4, 8 or 16 (the 64-bit route uses 8 for 16) */
     int32_t blocks_per_sm;      /* persistent-launch occupancy target */
-    uint64_t chunk;             /* numbers per chunk of a long stream (multiple
-                                   of threads_per_block*numbers_per_thread) */
+    uint64_t chunk;             /* maximum numbers per chunk of a long stream
+                                   (multiple of threads_per_block*numbers_per_thread);
+                                   the planner also cuts streams whose work
+                                   exceeds one resident block's share of the
+                                   launch, in whole tiles */
     int32_t require_safe;       /* p, q must be safe primes (Sec. V) */
     int32_t reserved[7];
 } rsaprng_config;

@@ -39,7 +39,7 @@ int cuda_fail(cudaError_t e, const char *what)
 }
 
 static const rsaprng_config kDefaultConfig = {
-    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_HYBRID, 128, 16, 0, 1ULL << 18, 0,
+    sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP, 128, 16, 0, 1ULL << 18, 0,
     {0, 0, 0, 0, 0, 0, 0}};
 
 static int check_config(const rsaprng_config &c)
@@ -141,8 +141,15 @@ static inline uint64_t cost_per_number(uint32_t e)
     return (uint64_t)(bl + __builtin_popcount(e) + 6);
 }
 
-int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
-               const uint64_t *offsets, uint64_t chunk, HostPlan &hp)
+// Pieces per resident block that the load balance aims for: the persistent
+// launch hands out items in decreasing cost, and an instance whose work is
+// larger than a block's fair share would otherwise finish alone at the end
+// of the launch. Every extra piece costs a skip-sum pass over the piece
+// before it, so the split is no finer than that.
+constexpr uint64_t kPiecesPerBlock = 1;
+
+int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
+               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp)
 {
     hp.items.clear();
     hp.chunks.clear();
@@ -152,12 +159,19 @@ int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint6
         chunk = ~0ULL;
     // Group requests by instance, keeping array order inside each instance.
     std::vector<uint64_t> order(nreq);
+    uint64_t work = 0;
     for (uint64_t i = 0; i < nreq; i++) {
         if (ids[i] >= c->count)
             return fail(RSAPRNG_ERR_ID, "request %llu: unknown instance id %u",
                         (unsigned long long)i, ids[i]);
         order[i] = i;
+        work += counts[i] * cost_per_number(c->h_params[ids[i]].e);
     }
+    // Cost of one piece: the work spread over the resident blocks of the
+    // launch, kPiecesPerBlock pieces each; pieces are whole tiles.
+    const GenLaunch full = ctx_launch(c, cfg, ~0ULL, true, false);
+    const uint64_t tile = (uint64_t)full.threads * full.L;
+    const uint64_t piece_cost = std::max<uint64_t>(1, work / ((uint64_t)full.grid * kPiecesPerBlock));
     std::stable_sort(order.begin(), order.end(),
                      [&](uint64_t x, uint64_t y) { return ids[x] < ids[y]; });
     struct Piece {
@@ -171,12 +185,20 @@ int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint6
         while (g1 < nreq && ids[order[g1]] == id)
             g1++;
         pieces.clear();
+        const uint64_t w = cost_per_number(c->h_params[id].e);
+        uint64_t total = 0;
+        for (uint64_t k = g0; k < g1; k++)
+            total += counts[order[k]];
+        const uint64_t npieces = (total * w + piece_cost - 1) / piece_cost;
+        uint64_t len = npieces > 1 ? (total + npieces - 1) / npieces : total;
+        len = (len + tile - 1) / tile * tile;
+        const uint64_t cut = std::max<uint64_t>(1, std::min(chunk, len));
         uint64_t off = 0;
         for (uint64_t k = g0; k < g1; k++) {
             const uint64_t r = order[k];
             uint64_t left = counts[r], out = offsets[r];
             while (left > 0) {
-                const uint64_t room = chunk - (off % chunk);
+                const uint64_t room = cut - (off % cut);
                 const uint64_t len = std::min(left, room);
                 pieces.push_back({off, len, out});
                 off += len;
@@ -188,7 +210,6 @@ int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint6
         if (pieces.empty())
             continue;
         hp.numbers += off;
-        const uint64_t w = cost_per_number(c->h_params[id].e);
         if (pieces.size() == 1) {
             WorkItem it{id, WI_FROM_STATE | WI_WRITEBACK, pieces[0].len, pieces[0].out, 0, 0};
             hp.items.push_back(it);
@@ -200,7 +221,8 @@ int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint6
         for (size_t k = 0; k < pieces.size(); k++) {
             const bool last = k + 1 == pieces.size();
             WorkItem it{id, last ? (uint32_t)WI_WRITEBACK : 0u, pieces[k].len, pieces[k].out, 0, 0};
-            PrepChunk pc{id, (uint32_t)hp.items.size(), pieces[k].offset, pieces[k].len};
+            // The last piece's skip sum is needed by no later piece.
+            PrepChunk pc{id, (uint32_t)hp.items.size(), pieces[k].offset, last ? 0 : pieces[k].len};
             hp.chunks.push_back(pc);
             hp.items.push_back(it);
             item_cost.push_back(pieces[k].len * w);
@@ -746,7 +768,7 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
     cudaSetDevice(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     HostPlan hp;
-    int rc = build_plan(c, nreq, ids, counts, out_offsets, c->cfg.chunk, hp);
+    int rc = build_plan(c, c->cfg, nreq, ids, counts, out_offsets, c->cfg.chunk, hp);
     if (rc)
         return rc;
     if (hp.items.empty())

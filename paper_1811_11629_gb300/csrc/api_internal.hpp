@@ -75,8 +75,8 @@ int cuda_fail(cudaError_t e, const char *what);
 DeviceTables ctx_tables(rsaprng_ctx *c);
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
                      bool want_c, int *occupancy = nullptr);
-int build_plan(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts,
-               const uint64_t *offsets, uint64_t chunk, HostPlan &hp);
+int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
+               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
                 uint64_t *d_c, cudaStream_t stream, uint64_t *launches);

@@ -55,12 +55,32 @@ __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 n)
     return (s < a || s >= n) ? s - n : s;
 }
 
-// s mod n for a skip s < Q: since n >= 2^62, Q < 2n.
-__device__ __forceinline__ u64 skip_mod_n(u64 s, u64 n) { return s >= n ? s - n : s; }
+// a + b as a 64-bit representative of the sum's class mod n, not reduced:
+// when the sum carries out of 64 bits, the dropped 2^64 is replaced by
+// r64 = 2^64 mod n. With b < 2^63 the wrapped sum is below b, and r64 < 2^63
+// (r64 = 2^64 - n for n > 2^63, else r64 < n < 2^63), so the second addition
+// cannot carry. Messages are kept this way inside a tile: the exponentiation
+// below needs only m mod p and m mod q, and n = 0 (mod p) and (mod q).
+__device__ __forceinline__ u64 add_cong(u64 a, u64 b, u64 r64)
+{
+    const u64 t = a + b;
+    return t < a ? t + r64 : t;
+}
 
-// Montgomery product a b 2^-32 mod p for a, b < p < 2^32, p odd, pinv =
-// p^-1 mod 2^32. With mq = T_lo pinv, mq p = T (mod 2^32) exactly, so
-// T - mq p = (T_hi - hi(mq p)) 2^32 and the difference lies in (-p, p).
+// x mod n for any 64-bit x: n >= 2^62, so x < 4n and three conditional
+// subtractions suffice.
+__device__ __forceinline__ u64 reduce_u64(u64 x, u64 n)
+{
+    x = x >= n ? x - n : x;
+    x = x >= n ? x - n : x;
+    return x >= n ? x - n : x;
+}
+
+// Montgomery reduction T 2^-32 mod p, p odd, pinv = p^-1 mod 2^32. With
+// mq = T_lo pinv, mq p = T (mod 2^32) exactly, so T - mq p = (T_hi - hi(mq p))
+// 2^32. hi(mq p) < p, so for any 64-bit T the result lies in [0, 2^32) and is
+// congruent to T 2^-32; it is below p whenever T_hi < p (T < p 2^32), in
+// particular for the product of any a < 2^32 with b < p.
 __device__ __forceinline__ u32 redc32(u64 T, u32 p, u32 pinv)
 {
     const u32 mq = (u32)T * pinv;
@@ -74,7 +94,9 @@ __device__ __forceinline__ u32 mont32(u32 a, u32 b, u32 p, u32 pinv)
     return redc32((u64)a * b, p, pinv);
 }
 
-// Montgomery product a b 2^-64 mod n for a, b < n, n odd, ninv = n^-1 mod 2^64.
+// Montgomery product a b 2^-64 mod n, n odd, ninv = n^-1 mod 2^64. For any
+// 64-bit a, b the result lies in [0, 2^64) and is congruent to a b 2^-64; it
+// is below n whenever one factor is below n.
 __device__ __forceinline__ u64 mont64(u64 a, u64 b, u64 n, u64 ninv)
 {
     const u64 lo = a * b;
@@ -90,6 +112,9 @@ __device__ __forceinline__ u64 mont64(u64 a, u64 b, u64 n, u64 ninv)
 // square-and-multiply runs on them with Montgomery products (Sec. I), the
 // constants kp = 2^(64e) mod p, kq remove the Montgomery factors, and Garner's
 // formula recombines: c = ((c_p - c_q) q^-1 mod p) q + c_q.
+// m_j may be any 64-bit representative of the message's class mod n: the
+// chain values stay below 2^32 and congruent, and the final product with
+// kp < p (kq < q) returns the fully reduced residue.
 template <int L>
 __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
 {
@@ -143,7 +168,8 @@ __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], cons
 
 // c_j = m_j^e mod n with 64-bit Montgomery products on the plain message:
 // the chain ends at m^e 2^(64(1-e)); the product with kn = 2^(64e) mod n
-// gives m^e mod n.
+// gives m^e mod n. As for the CRT route, m_j may be any 64-bit representative
+// mod n; the final product with kn < n is fully reduced.
 template <int L>
 __device__ __forceinline__ void encrypt_mont64(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
 {
@@ -171,11 +197,19 @@ __device__ __forceinline__ void encrypt_mont64(const u64 (&m)[L], u64 (&c)[L], c
 
 constexpr u64 ONE_MINUS_ULP_BITS = 0x3FEFFFFFFFFFFFFFULL;  // 1 - 2^-53
 
+// The 1.0 guard for a non-negative double: the bit patterns of non-negative
+// doubles are ordered as their values, so r >= 1.0 exactly when the pattern
+// exceeds that of 1 - 2^-53. Tested on the integer pipe, not the FP64 one.
+__device__ __forceinline__ double guard_below_one(double r)
+{
+    const u64 b = (u64)__double_as_longlong(r);
+    return __longlong_as_double((long long)(b > ONE_MINUS_ULP_BITS ? ONE_MINUS_ULP_BITS : b));
+}
+
 // r = RN(RN(c)/RN(n)) with IEEE double conversion and division; dn = RN(n).
 __device__ __forceinline__ double unit_fp64(u64 c, double dn)
 {
-    const double r = __ddiv_rn(__ull2double_rn(c), dn);
-    return r >= 1.0 ? __longlong_as_double((long long)ONE_MINUS_ULP_BITS) : r;
+    return guard_below_one(__ddiv_rn(__ull2double_rn(c), dn));
 }
 
 // The same value with the FP64 pipe but without a division: with the
@@ -190,8 +224,7 @@ __device__ __forceinline__ double unit_recip(u64 c, double dn, double y)
     const double C = __ull2double_rn(c);
     const double q0 = __dmul_rn(C, y);
     const double r = __fma_rn(-q0, dn, C);
-    const double q = __fma_rn(r, y, q0);
-    return q >= 1.0 ? __longlong_as_double((long long)ONE_MINUS_ULP_BITS) : q;
+    return guard_below_one(__fma_rn(r, y, q0));
 }
 
 // The same value from integers only. RN(c) = Mc 2^Ec is rounded to 53 bits

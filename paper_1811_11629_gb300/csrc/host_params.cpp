@@ -164,6 +164,7 @@ void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
     // the chain ends at m^e R^(1-e); one more product with R^e gives m^e.
     const u64 r64_mod_n = (u64)(((u128)1 << 64) % n);
     o.kn = powmod(r64_mod_n, e, n);
+    o.r64 = r64_mod_n;
     o.p = (u32)p;
     o.q = (u32)q;
     o.pinv = inv_mod_2_32((u32)p);

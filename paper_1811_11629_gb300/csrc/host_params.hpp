@@ -47,7 +47,7 @@ struct alignas(16) InstParams {
     u32 pad;
     double dn;       // RN(n) as a double
     double recip;    // RN(1 / RN(n)), the correctly rounded reciprocal
-    u64 pad2;
+    u64 r64;         // 2^64 mod n
 };
 static_assert(sizeof(InstParams) == 112, "InstParams layout");
 

@@ -4,9 +4,11 @@
 // outputs; thread t owns the L consecutive outputs tL+1 .. tL+L of a tile:
 //   1. skips: its first skip is s_tile a^(tL) (power table), then L steps of
 //      s <- a s mod Q with the 32-bit multiplier (Eq. congruentialgenerator1);
-//   2. messages: the skips (mod n) are summed per thread, a block-wide
-//      exclusive scan mod n gives each thread the message before its run,
-//      and a running carry links the tiles (Sec. IV, m_k = m_{k-1} + s_k);
+//   2. messages: the skips are summed per thread, a block-wide exclusive
+//      scan mod n gives each thread the message before its run, and a
+//      running carry links the tiles (Sec. IV, m_k = m_{k-1} + s_k); inside
+//      a thread's run the messages are 64-bit representatives mod n, not
+//      reduced, since step 3 needs only their residues mod p and mod q;
 //   3. encryption of the L messages as independent chains (Eq. encrypt2);
 //   4. r = c / n (Eq. CodeFloatingPointStep) and the 1.0 guard;
 //   5. outputs are staged in shared memory and written with coalesced stores.
@@ -20,10 +22,11 @@
 
 namespace rsaprng {
 
+using dev::add_cong;
 using dev::addmod;
 using dev::mulmodQ;
 using dev::mulmodQ_small;
-using dev::skip_mod_n;
+using dev::reduce_u64;
 
 namespace {
 
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
     while (it < nitems) {
         const WorkItem W = items[it];
         const InstParams P = tab.params[W.inst];
-        const u64 n = P.n;
+        const u64 n = P.n, r64 = P.r64;
         const u32 a = P.a;
         const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
         u64 m, s;
@@ -148,19 +151,20 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
 #pragma unroll
             for (int j = 0; j < L; j++) {
                 x = mulmodQ_small(x, a);
-                sk[j] = skip_mod_n(x, n);
+                sk[j] = x;
                 if (j < nvalid) {
-                    sum = addmod(sum, sk[j], n);
+                    sum = add_cong(sum, x, r64);
                     s_last = x;
                 }
             }
+            sum = reduce_u64(sum, n);
             u64 total;
             const u64 pre = block_exscan_mod(sum, n, sh_scan, total);
             u64 msg[L];
             u64 mm = addmod(m, pre, n);
 #pragma unroll
             for (int j = 0; j < L; j++) {
-                mm = addmod(mm, sk[j], n);
+                mm = add_cong(mm, sk[j], r64);
                 msg[j] = mm;
             }
             if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
@@ -210,6 +214,8 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
 // chunk_s[k] = s a^o mod Q (the skip before its first output) and
 // chunk_sum[k] = sum_{x=1..len} (s a^(o+x) mod Q) mod n, where s is the
 // instance's current skip. One block per chunk, 256 threads x 8 skips a tile.
+// The last chunk of an instance is listed with len = 0: no later chunk needs
+// its sum.
 constexpr int kPrepT = 256;
 constexpr int kPrepL = 8;
 __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
     for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
         const PrepChunk C = chunks[k];
         const InstParams P = tab.params[C.inst];
-        const u64 n = P.n;
+        const u64 n = P.n, r64 = P.r64;
         const u32 a = P.a;
         const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
         const u64 *p2k = tab.pow2k + (size_t)P.root * 64;
@@ -251,11 +257,11 @@ __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
             for (int j = 0; j < kPrepL; j++) {
                 x = mulmodQ_small(x, a);
                 if (j < nvalid)
-                    acc = addmod(acc, skip_mod_n(x, n), n);
+                    acc = add_cong(acc, x, r64);
             }
             s_thr = mulmodQ(s_thr, aS);
         }
-        const u64 tot = block_reduce_mod(acc, n, sh_scan);
+        const u64 tot = block_reduce_mod(reduce_u64(acc, n), n, sh_scan);
         if (t == 0)
             chunk_sum[k] = tot;
         __syncthreads();

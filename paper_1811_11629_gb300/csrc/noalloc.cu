@@ -85,7 +85,7 @@ __global__ void k_noalloc_plan(NoAllocScratch *S, uint32_t inst, uint64_t N, uin
     c.inst = inst;
     c.item = i;
     c.offset = off;
-    c.len = len;
+    c.len = last ? 0 : len;  // the last chunk's skip sum is needed by no later chunk
     S->chunks[i] = c;
 }
 

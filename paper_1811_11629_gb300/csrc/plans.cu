@@ -33,8 +33,9 @@ void destroy_graph(rsaprng_plan *p)
 int plan_create_cfg(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                     const uint64_t *counts, const uint64_t *offsets, rsaprng_plan **out)
 {
+    cudaSetDevice(c->device);
     HostPlan hp;
-    int rc = build_plan(c, nreq, ids, counts, offsets, cfg.chunk, hp);
+    int rc = build_plan(c, cfg, nreq, ids, counts, offsets, cfg.chunk, hp);
     if (rc)
         return rc;
     rsaprng_plan *p = new (std::nothrow) rsaprng_plan();

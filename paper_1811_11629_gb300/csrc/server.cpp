@@ -289,7 +289,8 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     chunk = std::max<uint64_t>(tile, (chunk + tile - 1) / tile * tile);
     chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(S->ctx->cfg.chunk, tile));
     HostPlan hp;
-    int rc = build_plan(S->ctx, ids.size(), ids.data(), counts.data(), offs.data(), chunk, hp);
+    int rc = build_plan(S->ctx, S->ctx->cfg, ids.size(), ids.data(), counts.data(), offs.data(),
+                        chunk, hp);
     if (rc == RSAPRNG_OK)
         rc = upload_plan(S->ctx, hp, sl.plan, sl.stream);
     if (rc == RSAPRNG_OK)
