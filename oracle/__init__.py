@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -90,6 +90,10 @@ def _configure(L):
         "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
                                    pu64, pu64, pu64, pdbl, i32]),
         "or_max_threads": (i32, []),
+        "or_digit_of_unit": (u64, [dbl, u64]),
+        "or_histogram": (i32, [ctypes.c_void_p, pu64, pu64, u64, u64, u64, i32, i32, pu64]),
+        "or_histogram_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64, u64,
+                                    u64, i32, i32, pu64]),
         "or_splitmix64_next": (u64, [pu64]),
         "or_params_from_seed": (i32, [u64, i32, u64, u64, pu64, pu64, pu64, pu64]),
     }
@@ -276,6 +280,26 @@ def generate_many(p, q, e, a, m, s, counts, offsets=None, route=ROUTE_CHECKED, w
     if rc != 0:
         raise RuntimeError(f"oracle generate_many failed ({rc})")
     return c, r
+
+
+def digit_of_unit(r: float, d: int) -> int:
+    """floor(r d), exactly, for a float output r in [0, 1) (Sec. VII's binning)."""
+    return lib().or_digit_of_unit(r, d)
+
+
+def histogram_many(p, q, e, a, m, s, counts, D, d, source=0, route=ROUTE_PAPER, q_mod=Q):
+    """Frequency (D = 1) / serial (D > 1) test histogram (Sec. VII) of the next counts[i]
+    outputs of each instance: non-overlapping D-tuples, bin = sum_i digit_i d^(i-1), digit
+    floor(r d) (source 0) or c mod d (source 1). m, s are advanced in place."""
+    p, q, e, a = (np.ascontiguousarray(x, dtype=np.uint64) for x in (p, q, e, a))
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    assert m.dtype == np.uint64 and s.dtype == np.uint64
+    hist = np.zeros(int(d) ** int(D), np.uint64)
+    rc = lib().or_histogram_many(len(counts), _p64(p), _p64(q), _p64(e), _p64(a), q_mod, _p64(m),
+                                 _p64(s), _p64(counts), D, d, source, route, _p64(hist))
+    if rc != 0:
+        raise RuntimeError(f"oracle histogram_many failed ({rc})")
+    return hist
 
 
 def max_threads() -> int:

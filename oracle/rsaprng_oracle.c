@@ -30,9 +30,15 @@
  *                                on tiny Q and by the two routes agreeing
  *   or_params_from_seed          pinned: SplitMix64 published test values
  *                                and the parameter rules re-checked by MR
+ *   or_digit_of_unit             pinned: exact-rational floor(r d) for
+ *                                power-of-two and decimal d, boundaries
+ *   or_histogram                 pinned: tuple counts rebuilt from the
+ *                                generated sequence, total = floor(N / D)
  */
+#include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -446,6 +452,108 @@ int or_generate_many(uint64_t count, const uint64_t *p, const uint64_t *q, const
 #pragma omp critical
             if (err == OR_OK)
                 err = rc;
+        }
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------ */
+/* Frequency and serial test histograms (Sec. VII)                      */
+/* ------------------------------------------------------------------ */
+
+/* floor(r d) for a double r in [0, 1) and an integer d < 2^32, exactly: r is
+ * f 2^x with f in [1/2, 1) holding at most 53 significant bits, so
+ * r = M / 2^(53 - x) with the integer M = f 2^53, and the floor of r d is the
+ * integer quotient (M d) >> (53 - x). */
+uint64_t or_digit_of_unit(double r, uint64_t d)
+{
+    if (r == 0.0)
+        return 0;
+    int x;
+    const double f = frexp(r, &x);
+    const uint64_t M = (uint64_t)ldexp(f, 53);
+    const int sh = 53 - x;
+    if (sh >= 128)
+        return 0;
+    return (uint64_t)(((u128)M * d) >> sh);
+}
+
+/*
+ * The histogram of the one-dimensional frequency test (D = 1) and the
+ * D-dimensional serial test (Sec. VII) over the next N outputs of one
+ * instance: the outputs are cut into non-overlapping D-tuples of consecutive
+ * outputs, each tuple (x_1, ..., x_D) adds one to
+ * hist[digit(x_1) + digit(x_2) d + ... + digit(x_D) d^(D-1)], with
+ * digit = floor(r d) of the float output (source 0) or c mod d of the
+ * ciphertext (source 1). Outputs after the last whole tuple are generated
+ * (the state advances by N) but not counted. hist has d^D entries and is
+ * added to.
+ */
+int or_histogram(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t N, uint64_t D,
+                 uint64_t d, int source, int route, uint64_t *hist)
+{
+    enum { BLK = 4096 };
+    uint64_t c[BLK];
+    double r[BLK];
+    uint64_t bin = 0, w = 1, filled = 0;
+    if (D < 1 || d < 2)
+        return OR_ERR_ARG;
+    for (uint64_t done = 0; done < N;) {
+        const uint64_t k = (N - done < BLK) ? N - done : BLK;
+        const int rc = or_generate(P, m_io, s_io, k, c, r, route);
+        if (rc != OR_OK)
+            return rc;
+        for (uint64_t i = 0; i < k; i++) {
+            const uint64_t g = (source == 0) ? or_digit_of_unit(r[i], d) : c[i] % d;
+            bin += g * w;
+            w *= d;
+            if (++filled == D) {
+                hist[bin]++;
+                bin = 0;
+                w = 1;
+                filled = 0;
+            }
+        }
+        done += k;
+    }
+    return OR_OK;
+}
+
+/* or_histogram over many instances (OpenMP over instances, one private
+ * histogram per thread, summed at the end); m[i], s[i] are advanced. */
+int or_histogram_many(uint64_t count, const uint64_t *p, const uint64_t *q, const uint64_t *e,
+                      const uint64_t *a, uint64_t Q, uint64_t *m, uint64_t *s,
+                      const uint64_t *counts, uint64_t D, uint64_t d, int source, int route,
+                      uint64_t *hist)
+{
+    uint64_t bins = 1;
+    for (uint64_t i = 0; i < D; i++)
+        bins *= d;
+    int err = OR_OK;
+#pragma omp parallel
+    {
+        uint64_t *mine = (uint64_t *)calloc(bins, sizeof(uint64_t));
+        if (!mine) {
+#pragma omp critical
+            err = OR_ERR_ARG;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < (int64_t)count; i++) {
+            if (!mine)
+                continue;
+            or_params P = {p[i], q[i], e[i], a[i], Q};
+            const int rc = or_histogram(&P, &m[i], &s[i], counts[i], D, d, source, route, mine);
+            if (rc != OR_OK) {
+#pragma omp critical
+                if (err == OR_OK)
+                    err = rc;
+            }
+        }
+        if (mine) {
+#pragma omp critical
+            for (uint64_t b = 0; b < bins; b++)
+                hist[b] += mine[b];
+            free(mine);
         }
     }
     return err;

@@ -141,8 +141,30 @@ def check_split(L):
                for mv in (2, 32, 1000) for g in (0, 1, mv - 1))
 
 
+def check_histogram(L):
+    # digits: exact floor(r d), e.g. 0.3 * 10 rounds to 3.0 but its floor is 2
+    for r, d in [(0.3, 10), (0.1, 10), (1 - 2.0 ** -53, 10), (0.7, 1000), (0.5, 1 << 20)]:
+        if L.or_digit_of_unit(r, d) != math.floor(Fraction(r) * d):
+            return False
+    # D = 2 tuples of a short sequence, rebuilt in Python
+    p, q, e, N, D, d = 2147483659, 2147483693, 5, 101, 2, 8
+    rc, c, r, _, _ = _gen(L, p, q, e, 777, 1, N)
+    if rc != 0:
+        return False
+    want = np.zeros(d ** D, np.uint64)
+    for k in range(N // D):
+        want[sum(math.floor(Fraction(float(r[k * D + i])) * d) * d ** i for i in range(D))] += 1
+    prm = P(p, q, e, A, Q)
+    m, s = ctypes.c_uint64(777), ctypes.c_uint64(1)
+    hist = np.zeros(d ** D, np.uint64)
+    if L.or_histogram(ctypes.byref(prm), ctypes.byref(m), ctypes.byref(s), N, D, d, 0, 0,
+                      hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))) != 0:
+        return False
+    return bool((hist == want).all())
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
-          check_rsa, check_unit, check_split]
+          check_rsa, check_unit, check_split, check_histogram]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -161,6 +183,10 @@ MUTANTS = {
     "split_off_by_one": ("u128 k = (u128)gamma * (u128)((Q - 1) / Mv);",
                          "u128 k = (u128)(gamma + 1) * (u128)((Q - 1) / Mv);"),
     "division_by_reciprocal": ("double r = dc / dn;", "double r = dc * (1.0 / dn);"),
+    "digit_rounded_product": ("return (uint64_t)(((u128)M * d) >> sh);",
+                              "return (uint64_t)(r * (double)d);"),
+    "tuple_digits_reversed": ("            bin += g * w;\n            w *= d;",
+                              "            bin = bin * d + g;"),
 }
 
 
@@ -183,7 +209,7 @@ def test_planted_mistake_is_caught(tmp_path, name):
     mutated.write_text(src.replace(before, after))
     so = tmp_path / "libmutant.so"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                    "-o", str(so), str(mutated)], check=True)
+                    "-o", str(so), str(mutated), "-lm"], check=True)
     L = oracle.load_library(str(so))
     failed = [chk.__name__ for chk in CHECKS if not chk(L)]
     assert failed, f"no pin catches the planted mistake {name}"
