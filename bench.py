@@ -59,6 +59,8 @@ def parse_args(argv=None):
                     help="override numbers per instance (small profiling runs only)")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--per-thread", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="cap on resident generation blocks per SM (0: occupancy limit)")
     ap.add_argument("--modexp", type=int, default=0)
     ap.add_argument("--divide", type=int, default=0)
     ap.add_argument("--e-rule", default="", choices=["", "smallest", "uniform", "at_least"],
@@ -339,6 +341,41 @@ def form_batched(R, torch, device, peak_alu, rank) -> dict:
     return res
 
 
+def form_fused(R, torch, device, peak_alu, rank) -> dict:
+    """Fused consumer: the bulk workload (1024 x 2^20, e uniform in [3, 65537]) binned into
+    the frequency-test histogram (D = 1, 2^20 bins) and the serial-test histogram (D = 2,
+    1024^2 bins) inside the generation kernel; nothing is written per output."""
+    cfg = workload.CONFIGS["bulk_1024x2^20"]
+    k, n = cfg["instances"], cfg["count"]
+    ctx = R.Context(k, device=device, chunk=n)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    ids = np.arange(first, first + k, dtype=np.uint32)
+    counts = np.full(k, n, np.uint64)
+    es = [ctx.params(int(i))[2] for i in ids]
+    out = {}
+    for name, D, d in (("frequency_2^20", 1, 1 << 20), ("serial_2d_1024^2", 2, 1024)):
+        hist = torch.zeros(d ** D, dtype=torch.int64, device="cuda")
+        ctx.histogram(ids, counts, D, d, R.HIST_HIGH, hist=hist)  # warm-up
+        reps = 3
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hist.zero_()
+        a.record()
+        for _ in range(reps):
+            ctx.histogram(ids, counts, D, d, R.HIST_HIGH, hist=hist)
+        b.record()
+        torch.cuda.synchronize()
+        dt = a.elapsed_time(b) / 1e3 / reps
+        chi2, tuples = R.chi2_uniform(hist)
+        out[name] = {"value": round(k * n / dt / 1e9, 3), "unit": UNIT,
+                     "ms_per_call": round(dt * 1e3, 3),
+                     "alu_frac": round(_slots(es, [n] * k) / dt / 1e9 / peak_alu, 4),
+                     "chi2_per_dof": round(chi2 / (d ** D - 1), 5), "tuples": tuples}
+        del hist
+    ctx.close()
+    return out
+
+
 def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
     [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
@@ -406,7 +443,8 @@ def run_ours(args) -> int:
     seeds = rank_seeds(cfg, dist.rank)
     knobs = {x: y for x, y in (("threads_per_block", args.threads),
                                ("numbers_per_thread", args.per_thread),
-                               ("modexp", args.modexp), ("divide", args.divide)) if y}
+                               ("modexp", args.modexp), ("divide", args.divide),
+                               ("blocks_per_sm", args.blocks_per_sm)) if y}
     ctx = R.Context(k, device=dist.local_rank, chunk=n, **knobs)
     first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
@@ -522,6 +560,7 @@ def run_ours(args) -> int:
             "plain_1x1e6": form_plain(R, torch, dist.local_rank, peak_alu, dist.rank),
             "batched_1e5_lognormal": form_batched(R, torch, dist.local_rank, peak_alu, dist.rank),
             "serving_1e6": form_served(R, torch, dist.local_rank, peak_alu, dist.rank),
+            "fused_histogram_bulk": form_fused(R, torch, dist.local_rank, peak_alu, dist.rank),
         }
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)

@@ -209,6 +209,41 @@ int rsaprng_generate_batch_host(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_i
                                 const uint64_t *counts, const uint64_t *out_offsets, double *h_r,
                                 uint64_t *h_c, void *stream);
 
+/* ------------------------------------------------ fused consumer (Sec. VII) */
+
+/* Digit sources of rsaprng_histogram. */
+enum {
+    RSAPRNG_HIST_HIGH = 0, /* digit = floor(r d), exact, of the float output r */
+    RSAPRNG_HIST_LOW = 1   /* digit = c mod d of the ciphertext c (d a power of two) */
+};
+
+/* The histogram of the paper's one-dimensional frequency test (D = 1) and
+ * D-dimensional serial test (Sec. VII), accumulated while generating: the
+ * next counts[i] outputs of instance ids[i] are generated (the instance
+ * advances by counts[i], exactly as with rsaprng_generate_batch) and are not
+ * stored; each request's outputs are cut into non-overlapping D-tuples of
+ * consecutive outputs (x_{kD+1}, ..., x_{kD+D}), k = 0, 1, ..., and tuple k
+ * adds one to d_hist[sum_{i=1..D} digit(x_{kD+i}) d^(i-1)]. Outputs after the
+ * last whole tuple of a request are generated but not counted.
+ *  - d_hist: DEVICE array of d^D uint64 counters, added to (not cleared);
+ *    the caller keeps every counter below 2^64.
+ *  - ids, counts: HOST arrays of nreq entries; an instance may appear in
+ *    only one request of a call.
+ *  - D in [1, 8], d >= 2, d^D <= 2^32; d a power of two for RSAPRNG_HIST_LOW.
+ * Asynchronous on stream. Errors: RSAPRNG_ERR_ARG (bad D, d, source,
+ * repeated id, NULL), RSAPRNG_ERR_ID, RSAPRNG_ERR_CUDA. */
+int rsaprng_histogram(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                      const uint64_t *counts, uint32_t D, uint32_t d, int source,
+                      uint64_t *d_hist, void *stream);
+
+/* chi^2 = sum_b (O_b - E)^2 / E of a HOST histogram of `bins` counts against
+ * the uniform expectation E = total / bins (Sec. VII compares the histograms
+ * with a uniform Poisson distribution; the p-value is the chi^2 survival
+ * function with bins - 1 degrees of freedom). *total (optional) receives the
+ * number of counted tuples. Errors: RSAPRNG_ERR_ARG (NULL, no bins, empty
+ * histogram). */
+int rsaprng_chi2_uniform(const uint64_t *h_hist, uint64_t bins, double *chi2, uint64_t *total);
+
 /* ------------------------------------------------ plans and CUDA graphs */
 
 /* A device-resident launch plan for a fixed set of requests (same meaning

@@ -12,11 +12,13 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DEFAULT_ROOT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_INT, DIVIDE_RECIP, E_AT_LEAST, E_SMALLEST, E_UNIFORM,
+                   HIST_HIGH, HIST_LOW,
                    MODEXP_CRT32, MODEXP_MONT64, Q, Config, RsaPrngError, Stats, check)
 
 __all__ = ["Context", "Plan", "Server", "Config", "RsaPrngError", "is_prime", "root_allowed",
            "params_from_seed", "Q", "DEFAULT_ROOT", "MODEXP_CRT32", "MODEXP_MONT64",
-           "DIVIDE_INT", "DIVIDE_FP64", "DIVIDE_HYBRID", "DIVIDE_RECIP", "E_SMALLEST", "E_UNIFORM", "E_AT_LEAST"]
+           "DIVIDE_INT", "DIVIDE_FP64", "DIVIDE_HYBRID", "DIVIDE_RECIP", "E_SMALLEST", "E_UNIFORM", "E_AT_LEAST",
+           "HIST_HIGH", "HIST_LOW", "chi2_uniform"]
 
 
 def _u64p(a: np.ndarray):
@@ -43,6 +45,19 @@ def _dptr(t):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("output must be a contiguous CUDA tensor")
     return t.data_ptr()
+
+
+def chi2_uniform(hist) -> tuple:
+    """(chi^2, counted tuples) of a histogram against the uniform expectation
+    (rsaprng_chi2_uniform); hist is a host array or a tensor (copied to the host)."""
+    if hasattr(hist, "cpu"):
+        hist = hist.cpu().numpy()
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    chi2 = ctypes.c_double()
+    total = ctypes.c_uint64()
+    check(_lib.load().rsaprng_chi2_uniform(_u64p(h), len(h), ctypes.byref(chi2),
+                                           ctypes.byref(total)), "chi2_uniform")
+    return chi2.value, total.value
 
 
 def is_prime(x: int) -> bool:
@@ -85,6 +100,7 @@ class Context:
                                         ctypes.byref(cfg) if cfg is not None else None),
               "ctx_create")
         self.h = h
+        self.device = device
 
     def close(self):
         if self.h:
@@ -220,6 +236,25 @@ class Context:
         check(self.L.rsaprng_generate_batch_host(self.h, len(ids), _u32p(ids), _u64p(counts),
                                                  _u64p(offsets), hp(h_r), hp(h_c),
                                                  _stream_ptr(stream)), "generate_batch_host")
+
+    def histogram(self, ids, counts, D: int, d: int, source: int = 0, hist=None, stream=None):
+        """Frequency (D = 1) / serial (D > 1) test histogram of the next counts[i] outputs
+        of ids[i] (rsaprng_histogram). hist: CUDA int64 tensor of d**D counters, added to;
+        allocated (zeros) when None. Returns hist."""
+        import torch
+
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        if len(ids) != len(counts):
+            raise ValueError("ids and counts differ in length")
+        bins = int(d) ** int(D)
+        if hist is None:
+            hist = torch.zeros(bins, dtype=torch.int64, device=f"cuda:{self.device}")
+        elif hist.dtype != torch.int64 or hist.numel() < bins:
+            raise ValueError(f"hist must be an int64 tensor of at least d**D = {bins} counters")
+        check(self.L.rsaprng_histogram(self.h, len(ids), _u32p(ids), _u64p(counts), D, d, source,
+                                       _dptr(hist), _stream_ptr(stream)), "histogram")
+        return hist
 
     def plan(self, ids, counts, offsets=None) -> "Plan":
         return Plan(self, ids, counts, offsets)

@@ -24,6 +24,7 @@ OK = 0
 MODEXP_AUTO, MODEXP_CRT32, MODEXP_MONT64 = 0, 1, 2
 DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_RECIP = 0, 1, 2, 3, 4
 E_SMALLEST, E_UNIFORM, E_AT_LEAST = 0, 1, 2
+HIST_HIGH, HIST_LOW = 0, 1
 Q = (1 << 63) - 25
 DEFAULT_ROOT = 2307085864
 
@@ -70,6 +71,8 @@ SIGNATURES = {
     "rsaprng_generate_f64_noalloc": (i32, [vp, u32, u64, vp, vp]),
     "rsaprng_generate_batch": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_generate_batch_host": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
+    "rsaprng_histogram": (i32, [vp, u64, pu32, pu64, u32, u32, i32, vp, vp]),
+    "rsaprng_chi2_uniform": (i32, [pu64, u64, pdbl, pu64]),
     "rsaprng_plan_create": (i32, [vp, u64, pu32, pu64, pu64, pvp]),
     "rsaprng_plan_launch": (i32, [vp, vp, vp, vp]),
     "rsaprng_plan_capture": (i32, [vp, vp, vp, vp]),

@@ -149,7 +149,8 @@ static inline uint64_t cost_per_number(uint32_t e)
 constexpr uint64_t kPiecesPerBlock = 1;
 
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
-               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp)
+               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
+               uint64_t tuple)
 {
     hp.items.clear();
     hp.chunks.clear();
@@ -170,8 +171,10 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
     // Cost of one piece: the work spread over the resident blocks of the
     // launch, kPiecesPerBlock pieces each; pieces are whole tiles.
     const GenLaunch full = ctx_launch(c, cfg, ~0ULL, true, false);
-    const uint64_t tile = (uint64_t)full.threads * full.L;
+    const uint64_t tile = (uint64_t)full.threads * full.L * std::max<uint64_t>(1, tuple);
     const uint64_t piece_cost = std::max<uint64_t>(1, work / ((uint64_t)full.grid * kPiecesPerBlock));
+    if (tuple > 1 && chunk != ~0ULL)
+        chunk = std::max(tile, chunk / tile * tile);
     std::stable_sort(order.begin(), order.end(),
                      [&](uint64_t x, uint64_t y) { return ids[x] < ids[y]; });
     struct Piece {
@@ -325,8 +328,23 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     return RSAPRNG_OK;
 }
 
+// Launch shape of the histogram consumer for cfg (its own occupancy).
+static GenLaunch hist_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems)
+{
+    GenLaunch g = ctx_launch(c, cfg, nitems, true, false);
+    int occ = hist_blocks_per_sm(g);
+    if (occ < 1)
+        occ = 1;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ)
+        occ = cfg.blocks_per_sm;
+    const uint64_t resident = (uint64_t)occ * c->sms;
+    g.persistent = nitems > resident;
+    g.grid = (int)(g.persistent ? resident : std::max<uint64_t>(nitems, 1));
+    return g;
+}
+
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
-                uint64_t *d_c, cudaStream_t stream, uint64_t *launches)
+                uint64_t *d_c, cudaStream_t stream, uint64_t *launches, const HistArgs *hist)
 {
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
@@ -341,15 +359,20 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         nl += 2;
     }
     if (dp.nitems) {
-        GenLaunch g = ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
+        GenLaunch g = hist ? hist_launch(c, cfg, dp.nitems)
+                           : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr,
+                                        &dp.occupancy);
         dp.last = g;
         if (g.persistent) {
             if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
                 return cuda_fail(e, "ticket reset");
         }
-        if ((e = launch_generate(g, t, dp.items, dp.nitems, dp.ticket, d_r, d_c, stream)) !=
-            cudaSuccess)
-            return cuda_fail(e, "generate launch");
+        if (hist)
+            e = launch_histogram(g, t, dp.items, dp.nitems, dp.ticket, *hist, stream);
+        else
+            e = launch_generate(g, t, dp.items, dp.nitems, dp.ticket, d_r, d_c, stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, hist ? "histogram launch" : "generate launch");
         nl += 1;
     }
     c->launches += nl;
@@ -782,6 +805,72 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
     cudaEventRecord(slot->done, st);
     slot->used = true;
     return rc;
+}
+
+int rsaprng_histogram(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
+                      const uint64_t *counts, uint32_t D, uint32_t d, int source,
+                      uint64_t *d_hist, void *stream)
+{
+    if (!c || (nreq && (!ids || !counts)) || !d_hist)
+        return fail(RSAPRNG_ERR_ARG, "histogram: null argument");
+    if (D < 1 || D > 8)
+        return fail(RSAPRNG_ERR_ARG, "histogram: D = %u not in [1, 8]", D);
+    if (source != RSAPRNG_HIST_HIGH && source != RSAPRNG_HIST_LOW)
+        return fail(RSAPRNG_ERR_ARG, "histogram: unknown source %d", source);
+    if (d < 2 || (source == RSAPRNG_HIST_LOW && (d & (d - 1))))
+        return fail(RSAPRNG_ERR_ARG, "histogram: d = %u (>= 2; a power of two for low bits)", d);
+    uint64_t bins = 1;
+    for (uint32_t i = 0; i < D; i++) {
+        bins *= d;
+        if (bins > (1ULL << 32))
+            return fail(RSAPRNG_ERR_ARG, "histogram: d^D above 2^32");
+    }
+    std::vector<rsaprng_id> sorted(ids, ids + nreq);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return fail(RSAPRNG_ERR_ARG, "histogram: an instance appears in two requests");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Tuples are counted from each request's start: every request is placed
+    // at offset 0, so a piece's offset is its position in its request.
+    const std::vector<uint64_t> zero(nreq, 0);
+    HostPlan hp;
+    int rc = build_plan(c, c->cfg, nreq, ids, counts, zero.data(), c->cfg.chunk, hp, D);
+    if (rc)
+        return rc;
+    if (hp.items.empty())
+        return RSAPRNG_OK;
+    ScratchSlot *slot;
+    if ((rc = scratch_slot(c, &slot)) != RSAPRNG_OK)
+        return rc;
+    if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
+        return rc;
+    const HistArgs h{(unsigned long long *)d_hist, d, D, source == RSAPRNG_HIST_LOW ? 1u : 0u, 0u};
+    rc = launch_plan(c, c->cfg, slot->plan, nullptr, nullptr, st, nullptr, &h);
+    cudaEventRecord(slot->done, st);
+    slot->used = true;
+    return rc;
+}
+
+int rsaprng_chi2_uniform(const uint64_t *h_hist, uint64_t bins, double *chi2, uint64_t *total)
+{
+    if (!h_hist || bins == 0 || !chi2)
+        return fail(RSAPRNG_ERR_ARG, "chi2_uniform: null argument or no bins");
+    // chi^2 = sum (O - E)^2 / E with E = t / bins equals bins sum O^2 / t - t;
+    // t and sum O^2 are exact integers.
+    unsigned __int128 s2 = 0;
+    uint64_t t = 0;
+    for (uint64_t i = 0; i < bins; i++) {
+        t += h_hist[i];
+        s2 += (unsigned __int128)h_hist[i] * h_hist[i];
+    }
+    if (t == 0)
+        return fail(RSAPRNG_ERR_ARG, "chi2_uniform: empty histogram");
+    const long double x = (long double)s2 * (long double)bins / (long double)t - (long double)t;
+    *chi2 = (double)x;
+    if (total)
+        *total = t;
+    return RSAPRNG_OK;
 }
 
 // Splits one instance's N outputs into chunks sized so that every SM gets

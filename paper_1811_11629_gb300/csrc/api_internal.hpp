@@ -75,11 +75,17 @@ int cuda_fail(cudaError_t e, const char *what);
 DeviceTables ctx_tables(rsaprng_ctx *c);
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
                      bool want_c, int *occupancy = nullptr);
+// Pieces of a stream are whole tiles; with tuple > 1 they are also whole
+// multiples of tuple outputs (the histogram consumer's D-tuples).
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
-               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp);
+               const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
+               uint64_t tuple = 1);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
+// Launches the pre-pass and the generation kernel, or the histogram
+// consumer instead of the generation kernel when hist is given.
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
-                uint64_t *d_c, cudaStream_t stream, uint64_t *launches);
+                uint64_t *d_c, cudaStream_t stream, uint64_t *launches,
+                const HistArgs *hist = nullptr);
 void free_devplan(DevPlan &dp);
 int scratch_slot(rsaprng_ctx *c, ScratchSlot **out);
 

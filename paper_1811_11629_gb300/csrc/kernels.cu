@@ -19,6 +19,7 @@
 
 #include "device_math.cuh"
 #include "kernels.cuh"
+#include "tile.cuh"
 
 namespace rsaprng {
 
@@ -30,76 +31,10 @@ using dev::reduce_u64;
 
 namespace {
 
-constexpr unsigned FULL = 0xFFFFFFFFu;
-
-// Padded shared-memory index: one 8-byte slot of padding every 16 elements
-// spreads the stride-L writes of a warp over the banks.
-__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
-
-// Block-wide exclusive scan of v (mod n). Returns the exclusive prefix and
-// the block total. sh must hold 32 entries. Contains two __syncthreads().
-__device__ __forceinline__ u64 block_exscan_mod(u64 v, u64 n, u64 *sh, u64 &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    u64 incl = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const u64 o = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d)
-            incl = addmod(incl, o, n);
-    }
-    if (lane == 31)
-        sh[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        u64 w = lane < nwarps ? sh[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const u64 o = __shfl_up_sync(FULL, w, d);
-            if (lane >= d)
-                w = addmod(w, o, n);
-        }
-        sh[lane] = w;
-    }
-    __syncthreads();
-    total = sh[nwarps - 1];
-    const u64 wpre = warp > 0 ? sh[warp - 1] : 0;
-    u64 ex = __shfl_up_sync(FULL, incl, 1);
-    if (lane == 0)
-        ex = 0;
-    return addmod(wpre, ex, n);
-}
-
-__device__ __forceinline__ u64 block_reduce_mod(u64 v, u64 n, u64 *sh)
-{
-    u64 total;
-    (void)block_exscan_mod(v, n, sh, total);
-    return total;
-}
-
-template <int L, int MODEXP>
-__device__ __forceinline__ void encrypt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
-{
-    if constexpr (MODEXP == MODEXP_CRT32)
-        dev::encrypt_crt<L>(m, c, P);
-    else
-        dev::encrypt_mont64<L>(m, c, P);
-}
-
-// Division route for output j of a thread's run.
-template <int DIV>
-__device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
-{
-    if constexpr (DIV == DIVIDE_INT)
-        return dev::unit_int_fast(c, P);
-    else if constexpr (DIV == DIVIDE_FP64)
-        return dev::unit_fp64(c, P.dn);
-    else if constexpr (DIV == DIVIDE_RECIP)
-        return dev::unit_recip(c, P.dn, P.recip);
-    else
-        return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_recip(c, P.dn, P.recip);
-}
+using tile::block_exscan_mod;
+using tile::block_reduce_mod;
+using tile::sidx;
+using tile::to_unit;
 
 template <int L, int MODEXP, int DIV>
 __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
@@ -126,8 +61,7 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
     while (it < nitems) {
         const WorkItem W = items[it];
         const InstParams P = tab.params[W.inst];
-        const u64 n = P.n, r64 = P.r64;
-        const u32 a = P.a;
+        const u64 n = P.n;
         const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
         u64 m, s;
         if (W.flags & WI_FROM_STATE) {
@@ -146,31 +80,9 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
             const int tile_n = left < (u64)S ? (int)left : S;
             const int my0 = t * L;
             const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0);
-            u64 sk[L];
-            u64 x = s_thr, sum = 0, s_last = 0;
-#pragma unroll
-            for (int j = 0; j < L; j++) {
-                x = mulmodQ_small(x, a);
-                sk[j] = x;
-                if (j < nvalid) {
-                    sum = add_cong(sum, x, r64);
-                    s_last = x;
-                }
-            }
-            sum = reduce_u64(sum, n);
-            u64 total;
-            const u64 pre = block_exscan_mod(sum, n, sh_scan, total);
-            u64 msg[L];
-            u64 mm = addmod(m, pre, n);
-#pragma unroll
-            for (int j = 0; j < L; j++) {
-                mm = add_cong(mm, sk[j], r64);
-                msg[j] = mm;
-            }
-            if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
-                tab.state_s[W.inst] = s_last;  // this thread owns the stream's last output
-            u64 c[L];
-            encrypt<L, MODEXP>(msg, c, P);
+            u64 c[L], total;
+            tile::tile_ciphertexts<L, MODEXP>(tab, W, P, m, s_thr, left, my0, nvalid, sh_scan, c,
+                                              total);
 #pragma unroll
             for (int j = 0; j < L; j++) {
                 const int i = sidx(my0 + j);

@@ -75,6 +75,21 @@ struct GenLaunch {
 // Shared memory bytes the generation kernel needs for a tile.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
 
+// Histogram consumer: d^D counters at hist; digits of r (low = 0) or of the
+// low bits of c (low = 1, d a power of two); D in [1, 8].
+struct HistArgs {
+    unsigned long long *hist;
+    uint32_t d;
+    uint32_t D;
+    uint32_t low;
+    uint32_t pad;
+};
+size_t hist_smem_bytes(int threads, int L);
+cudaError_t launch_histogram(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                             uint32_t nitems, uint32_t *ticket, const HistArgs &h,
+                             cudaStream_t stream);
+int hist_blocks_per_sm(const GenLaunch &g);
+
 cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                             uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
                             cudaStream_t stream);

@@ -1,0 +1,132 @@
+// Device building blocks of the tile engine shared by the generation kernel
+// and the fused consumers (arXiv:1811.11629 Sec. IV-V): the block scan of
+// skips mod n, the division route, and steps 1-3 of a tile.
+#pragma once
+#include <cstdint>
+
+#include "device_math.cuh"
+#include "kernels.cuh"
+
+namespace rsaprng {
+namespace tile {
+
+using dev::add_cong;
+using dev::addmod;
+using dev::mulmodQ;
+using dev::mulmodQ_small;
+using dev::reduce_u64;
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Padded shared-memory index: one 8-byte slot of padding every 16 elements
+// spreads the stride-L writes of a warp over the banks.
+__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
+
+// Block-wide exclusive scan of v (mod n). Returns the exclusive prefix and
+// the block total. sh must hold 32 entries. Contains two __syncthreads().
+__device__ __forceinline__ u64 block_exscan_mod(u64 v, u64 n, u64 *sh, u64 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    u64 incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const u64 o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d)
+            incl = addmod(incl, o, n);
+    }
+    if (lane == 31)
+        sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        u64 w = lane < nwarps ? sh[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const u64 o = __shfl_up_sync(FULL, w, d);
+            if (lane >= d)
+                w = addmod(w, o, n);
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    total = sh[nwarps - 1];
+    const u64 wpre = warp > 0 ? sh[warp - 1] : 0;
+    u64 ex = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0)
+        ex = 0;
+    return addmod(wpre, ex, n);
+}
+
+__device__ __forceinline__ u64 block_reduce_mod(u64 v, u64 n, u64 *sh)
+{
+    u64 total;
+    (void)block_exscan_mod(v, n, sh, total);
+    return total;
+}
+
+template <int L, int MODEXP>
+__device__ __forceinline__ void encrypt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
+{
+    if constexpr (MODEXP == MODEXP_CRT32)
+        dev::encrypt_crt<L>(m, c, P);
+    else
+        dev::encrypt_mont64<L>(m, c, P);
+}
+
+// Division route for output j of a thread's run.
+template <int DIV>
+__device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
+{
+    if constexpr (DIV == DIVIDE_INT)
+        return dev::unit_int_fast(c, P);
+    else if constexpr (DIV == DIVIDE_FP64)
+        return dev::unit_fp64(c, P.dn);
+    else if constexpr (DIV == DIVIDE_RECIP)
+        return dev::unit_recip(c, P.dn, P.recip);
+    else
+        return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_recip(c, P.dn, P.recip);
+}
+
+// Steps 1-3 of a tile for the calling thread, which owns outputs my0+1 ..
+// my0+L of the tile: its skips from s_thr (the skip before its run), the
+// block scan of their sums mod n, its messages from the carry m (the message
+// before the tile), and their L ciphertexts. Entries at or past nvalid are
+// computed but meaningless. The thread that owns the stream's last output
+// (left = outputs from the tile start to the end of the work item) writes the
+// instance's skip back when the item asks for it. total returns the tile's
+// skip sum mod n (the carry to the next tile). Contains two __syncthreads().
+template <int L, int MODEXP>
+__device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const WorkItem &W,
+                                                 const InstParams &P, u64 m, u64 s_thr, u64 left,
+                                                 int my0, int nvalid, u64 *sh_scan, u64 (&c)[L],
+                                                 u64 &total)
+{
+    const u64 n = P.n, r64 = P.r64;
+    const u32 a = P.a;
+    u64 sk[L];
+    u64 x = s_thr, sum = 0, s_last = 0;
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        x = mulmodQ_small(x, a);
+        sk[j] = x;
+        if (j < nvalid) {
+            sum = add_cong(sum, x, r64);
+            s_last = x;
+        }
+    }
+    sum = reduce_u64(sum, n);
+    const u64 pre = block_exscan_mod(sum, n, sh_scan, total);
+    u64 msg[L];
+    u64 mm = addmod(m, pre, n);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        mm = add_cong(mm, sk[j], r64);
+        msg[j] = mm;
+    }
+    if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
+        tab.state_s[W.inst] = s_last;  // this thread owns the stream's last output
+    encrypt<L, MODEXP>(msg, c, P);
+}
+
+}  // namespace tile
+}  // namespace rsaprng

@@ -89,3 +89,18 @@ def test_parameter_validation_codes(R):
     # a prime whose (p-1)/2 is composite fails the safe-prime rule of Sec. V
     assert not R.is_prime((p - 1) // 2) or not R.is_prime((q - 1) // 2)
     assert R.validate_params(p, q, e_ok, require_safe=True) == C["ERR_NOT_PRIME"]
+
+
+def test_chi2_uniform_host_helper(R):
+    """rsaprng_chi2_uniform against the chi^2 sum written out with numpy."""
+    rng = np.random.default_rng(3)
+    h = rng.integers(0, 50, 4096).astype(np.uint64)
+    chi2, total = R.chi2_uniform(h)
+    E = h.sum() / len(h)
+    want = float(((h.astype(np.float64) - E) ** 2 / E).sum())
+    assert total == int(h.sum())
+    assert abs(chi2 - want) <= 1e-9 * max(1.0, want)
+    flat = np.full(64, 9, np.uint64)
+    assert R.chi2_uniform(flat) == (0.0, 576)
+    with pytest.raises(R.RsaPrngError):
+        R.chi2_uniform(np.zeros(8, np.uint64))
