@@ -192,10 +192,11 @@ def imad_slots_per_number(e: int) -> int:
     chain products (squarings, multiplies and the final correction, for p and
     q) and the Garner product (1) = 5 (2k + 1) slots; REDC of m for p and q
     (2 x (1 + 2)); the skip a*s mod Q (two widening products and 25*H: 5);
-    Garner's h*q (2); the integer division (three widening products: 6).
+    Garner's h*q (2). The division r = c / n is the method's one floating-point
+    step and is not counted (the default route runs it on the FP64 pipe).
     """
     k = e.bit_length() + bin(e).count("1") - 1
-    return 5 * (2 * k + 1) + 6 + 5 + 2 + 6
+    return 5 * (2 * k + 1) + 6 + 5 + 2
 
 
 KERNEL_SOURCES = ["paper_1811_11629_gb300/csrc/kernels.cu",
