@@ -80,6 +80,8 @@ def _configure(L):
         "or_split_s0": (u64, [u64, u64, u64, u64, u64]),
         "or_encrypt_direct": (u64, [u64, u64, u64]),
         "or_crt_encrypt": (u64, [u64, u64, u64, u64, u64, u64]),
+        "or_crt_encrypt2": (u64, [u64, u64, u64, u64, u64, u64, u64]),
+        "or_crt_exponent": (u64, [u64, u64, u64, u64]),
         "or_unit": (dbl, [u64, u64]),
         "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
         "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
@@ -113,7 +115,7 @@ def _pd(a: np.ndarray):
 
 class _Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint64), ("q", ctypes.c_uint64), ("e", ctypes.c_uint64),
-                ("a", ctypes.c_uint64), ("Q", ctypes.c_uint64)]
+                ("a", ctypes.c_uint64), ("Q", ctypes.c_uint64), ("eq", ctypes.c_uint64)]
 
 
 # --- thin wrappers (one per C function) ---------------------------------------------
@@ -200,12 +202,13 @@ def params_from_seed(seed: int, e_rule: int = E_SMALLEST, e_lo: int = 3, e_hi: i
 
 
 def generate(p, q, e, m0, s0, count, a=2307085864, q_mod=Q, route=ROUTE_CHECKED, want_c=True,
-             want_r=True):
+             want_r=True, eq=0):
     """Outputs k = 1..count of one instance from state (m0, s0) (Eq. algorithm1).
 
+    eq: exponent of the q residue (CRT exponents, Sec. V's note); 0 means eq = e.
     Returns (c, r, m_end, s_end); c is uint64, r float64 (None when not wanted).
     """
-    P = _Params(p, q, e, a, q_mod)
+    P = _Params(p, q, e, a, q_mod, eq)
     m = ctypes.c_uint64(m0)
     s = ctypes.c_uint64(s0)
     c = np.empty(count, np.uint64) if want_c else None
@@ -216,6 +219,16 @@ def generate(p, q, e, m0, s0, count, a=2307085864, q_mod=Q, route=ROUTE_CHECKED,
     if rc != 0:
         raise RuntimeError(f"oracle generate failed ({rc})")
     return c, r, m.value, s.value
+
+
+def crt_exponent(p, q, ep, eq) -> int:
+    """E = ep mod (p-1), E = eq mod (q-1), or 0 when no such E exists (Sec. V's note)."""
+    return lib().or_crt_exponent(p, q, ep, eq)
+
+
+def crt_encrypt2(mp, mq, p, q, ep, eq) -> int:
+    """CRT(mp^ep mod p, mq^eq mod q) by Garner's formula."""
+    return lib().or_crt_encrypt2(mp, mq, p, q, ep, eq, lib().or_invmod(q % p, p))
 
 
 def seek(p, q, a, m0, s0, k, q_mod=Q):

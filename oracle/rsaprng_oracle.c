@@ -24,6 +24,9 @@
  *   or_skip_next_*               pinned: closed form s_k = s_0 a^k mod Q and
  *                                the period structure of Sec. IV (tiny Q)
  *   or_crt_encrypt               pinned: CRT residues, Garner reconstruction
+ *   or_crt_encrypt2 / or_crt_exponent
+ *                                pinned: residue-wise powers, m^E mod n with
+ *                                E from a Python CRT, permutation of Z_n
  *   or_unit                      pinned: exact-rational rounding of the two
  *                                IEEE conversions and the division
  *   or_generate (sequence)       pinned by the closed form of Eq. pseudoskip
@@ -244,18 +247,45 @@ uint64_t or_encrypt_direct(uint64_t m, uint64_t e, uint64_t n)
 }
 
 /* c from the residues m_p, m_q by CRT and Garner's formula (steps
- * CodeExponentiationStep1-3 of Eq. algorithm1): c_p = m_p^e mod p,
- * c_q = m_q^e mod q, c = (((c_p - c_q) q^{-1} mod p) mod p) q + c_q.
- * The difference is formed as (c_p + p - (c_q mod p)) so it never goes
- * negative (c_q can exceed p when q > p). */
-uint64_t or_crt_encrypt(uint64_t mp, uint64_t mq, uint64_t p, uint64_t q, uint64_t e,
-                        uint64_t qinv_p)
+ * CodeExponentiationStep1-3 of Eq. algorithm1): c_p = m_p^ep mod p,
+ * c_q = m_q^eq mod q, c = (((c_p - c_q) q^{-1} mod p) mod p) q + c_q, with
+ * ep = eq = e for the ordinary generator. The difference is formed as
+ * (c_p + p - (c_q mod p)) so it never goes negative (c_q can exceed p when
+ * q > p). */
+uint64_t or_crt_encrypt2(uint64_t mp, uint64_t mq, uint64_t p, uint64_t q, uint64_t ep,
+                         uint64_t eq, uint64_t qinv_p)
 {
-    uint64_t cp = or_powmod_native32(mp, e, p);
-    uint64_t cq = or_powmod_native32(mq, e, q);
+    uint64_t cp = or_powmod_native32(mp, ep, p);
+    uint64_t cq = or_powmod_native32(mq, eq, q);
     uint64_t diff = (cp + p - (cq % p)) % p;
     uint64_t h = (diff * qinv_p) % p;
     return h * q + cq;
+}
+
+uint64_t or_crt_encrypt(uint64_t mp, uint64_t mq, uint64_t p, uint64_t q, uint64_t e,
+                        uint64_t qinv_p)
+{
+    return or_crt_encrypt2(mp, mq, p, q, e, e, qinv_p);
+}
+
+/* The single exponent of CRT exponents (the paper's note on large exponents,
+ * Sec. V): E with E = ep (mod p-1) and E = eq (mod q-1), 0 <= E <
+ * lcm(p-1, q-1), by the CRT for the moduli p-1 and q-1 (not coprime: a
+ * solution exists iff ep = eq mod gcd(p-1, q-1)). Returns 0 when there is
+ * none (E itself is never 0: E = ep >= 1 mod p-1). */
+uint64_t or_crt_exponent(uint64_t p, uint64_t q, uint64_t ep, uint64_t eq)
+{
+    const uint64_t a = p - 1, b = q - 1;
+    const uint64_t g = or_gcd(a, b);
+    const uint64_t ra = ep % a, rb = eq % b;
+    const uint64_t diff = (rb + b - (ra % b)) % b; /* eq - ep mod b */
+    if (diff % g != 0)
+        return 0;
+    /* E = ra + a t with a t = diff (mod b): t = (diff / g) (a / g)^-1 mod (b / g) */
+    const uint64_t bg = b / g;
+    const uint64_t inv = (bg == 1) ? 0 : or_invmod((a / g) % bg, bg);
+    const uint64_t t = (bg == 1) ? 0 : (uint64_t)(((u128)((diff / g) % bg) * inv) % bg);
+    return ra + a * t; /* < a (b / g) = lcm(a, b) < 2^64 */
 }
 
 /* ------------------------------------------------------------------ */
@@ -279,8 +309,9 @@ double or_unit(uint64_t c, uint64_t n)
 /* One generator instance (Sec. IV state {n, e, Q, a} + {m, s})         */
 /* ------------------------------------------------------------------ */
 
+/* eq: the exponent of the q residue (CRT exponents); 0 means eq = e. */
 typedef struct {
-    uint64_t p, q, e, a, Q;
+    uint64_t p, q, e, a, Q, eq;
 } or_params;
 
 enum { OR_ROUTE_CHECKED = 0, OR_ROUTE_PAPER = 1, OR_ROUTE_DIRECT = 2 };
@@ -301,14 +332,19 @@ int or_generate(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t N,
                 uint64_t *c_out, double *r_out, int route)
 {
     const uint64_t p = P->p, q = P->q, e = P->e, a = P->a, Q = P->Q;
+    const uint64_t eq = P->eq ? P->eq : e;
     const uint64_t n = p * q;
     uint64_t m = *m_io, s = *s_io;
     uint64_t mp = m % p, mq = m % q;
     const uint64_t qinv_p = or_invmod(q % p, p);
     const int schrage_ok = (Q % a) < (Q / a);
-    if (p < 2 || q < 2 || a < 2 || a >= Q || m >= n || s == 0 || s >= Q)
+    /* The direct route needs one exponent: e itself, or the CRT exponent. */
+    const uint64_t E = (eq == e) ? e : or_crt_exponent(p, q, e, eq);
+    if (p < 2 || q < 2 || a < 1 || a >= Q || m >= n || s == 0 || s >= Q)
         return OR_ERR_ARG;
     if (route != OR_ROUTE_DIRECT && (p >= ((uint64_t)1 << 32) || q >= ((uint64_t)1 << 32) || !schrage_ok || qinv_p == 0))
+        return OR_ERR_ARG;
+    if (route == OR_ROUTE_DIRECT && E == 0)
         return OR_ERR_ARG;
 
     for (uint64_t k = 0; k < N; k++) {
@@ -317,11 +353,11 @@ int or_generate(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t N,
             s = or_skip_next_schrage(s, a, Q);
             mp = (mp + s) % p;
             mq = (mq + s) % q;
-            c = or_crt_encrypt(mp, mq, p, q, e, qinv_p);
+            c = or_crt_encrypt2(mp, mq, p, q, e, eq, qinv_p);
         } else if (route == OR_ROUTE_DIRECT) {
             s = or_skip_next_direct(s, a, Q);
             m = or_addmod(m, s % n, n);
-            c = or_encrypt_direct(m, e, n);
+            c = or_encrypt_direct(m, E, n);
         } else {
             uint64_t s_direct = or_skip_next_direct(s, a, Q);
             uint64_t s_paper = or_skip_next_schrage(s, a, Q);
@@ -333,11 +369,10 @@ int or_generate(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t N,
             mq = (mq + s) % q;
             if (m % p != mp || m % q != mq)
                 return OR_ERR_ROUTE_MISMATCH;
-            uint64_t c_direct = or_encrypt_direct(m, e, n);
-            uint64_t c_paper = or_crt_encrypt(mp, mq, p, q, e, qinv_p);
-            if (c_direct != c_paper)
+            uint64_t c_paper = or_crt_encrypt2(mp, mq, p, q, e, eq, qinv_p);
+            if (E != 0 && or_encrypt_direct(m, E, n) != c_paper)
                 return OR_ERR_ROUTE_MISMATCH;
-            c = c_direct;
+            c = c_paper;
         }
         if (c_out)
             c_out[k] = c;
@@ -411,7 +446,7 @@ int or_sample_many(uint64_t count, const uint64_t *p, const uint64_t *q, const u
     int err = OR_OK;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < (int64_t)count; i++) {
-        or_params P = {p[i], q[i], e[i], a[i], Q};
+        or_params P = {p[i], q[i], e[i], a[i], Q, 0};
         int rc = or_sample(&P, &m[i], &s[i], ks + koff[i], nk[i], c_out ? c_out + koff[i] : NULL,
                            r_out ? r_out + koff[i] : NULL);
         if (rc != OR_OK) {
@@ -445,7 +480,7 @@ int or_generate_many(uint64_t count, const uint64_t *p, const uint64_t *q, const
     int err = OR_OK;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < (int64_t)count; i++) {
-        or_params P = {p[i], q[i], e[i], a[i], Q};
+        or_params P = {p[i], q[i], e[i], a[i], Q, 0};
         int rc = or_generate(&P, &m[i], &s[i], counts[i], c_out ? c_out + offsets[i] : NULL,
                              r_out ? r_out + offsets[i] : NULL, route);
         if (rc != OR_OK) {
@@ -541,7 +576,7 @@ int or_histogram_many(uint64_t count, const uint64_t *p, const uint64_t *q, cons
         for (int64_t i = 0; i < (int64_t)count; i++) {
             if (!mine)
                 continue;
-            or_params P = {p[i], q[i], e[i], a[i], Q};
+            or_params P = {p[i], q[i], e[i], a[i], Q, 0};
             const int rc = or_histogram(&P, &m[i], &s[i], counts[i], D, d, source, route, mine);
             if (rc != OR_OK) {
 #pragma omp critical

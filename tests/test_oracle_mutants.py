@@ -24,7 +24,7 @@ A = 2307085864
 
 class P(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint64), ("q", ctypes.c_uint64), ("e", ctypes.c_uint64),
-                ("a", ctypes.c_uint64), ("Q", ctypes.c_uint64)]
+                ("a", ctypes.c_uint64), ("Q", ctypes.c_uint64), ("eq", ctypes.c_uint64)]
 
 
 def _gen(L, p, q, e, m0, s0, n, a=A, qm=Q, route=0):
@@ -163,8 +163,38 @@ def check_histogram(L):
     return bool((hist == want).all())
 
 
+def _crt_e(p, q, ep, eq):
+    a, b = p - 1, q - 1
+    g = math.gcd(a, b)
+    if (eq - ep) % g:
+        return 0
+    t = ((eq - ep) // g) * pow(a // g, -1, b // g) % (b // g) if b // g > 1 else 0
+    return (ep + a * t) % (a // g * b)
+
+
+def check_modes(L):
+    p, q, e = 2147483659, 2147483693, 5
+    n = p * q
+    # unit skip (a = 1): counter mode m_k = m_0 + k
+    rc, c, _, _, _ = _gen(L, p, q, e, 123, 1, 50, a=1)
+    if rc != 0 or any(int(c[k - 1]) != pow((123 + k) % n, e, n) for k in range(1, 51)):
+        return False
+    # CRT exponents: residue-wise powers and the single exponent
+    ep = next(x for x in range(3, 99, 2) if math.gcd(x, p - 1) == 1)
+    eq = next(x for x in range(ep + 2, 199, 2) if math.gcd(x, q - 1) == 1)
+    if L.or_crt_exponent(p, q, ep, eq) != _crt_e(p, q, ep, eq):
+        return False
+    inv = pow(q, -1, p)
+    rng = random.Random(9)
+    for m in [0, 1, n - 1] + [rng.randrange(n) for _ in range(50)]:
+        c = L.or_crt_encrypt2(m % p, m % q, p, q, ep, eq, inv)
+        if c % p != pow(m % p, ep, p) or c % q != pow(m % q, eq, q) or c >= n:
+            return False
+    return True
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
-          check_rsa, check_unit, check_split, check_histogram]
+          check_rsa, check_unit, check_split, check_histogram, check_modes]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -187,6 +217,10 @@ MUTANTS = {
                               "return (uint64_t)(r * (double)d);"),
     "tuple_digits_reversed": ("            bin += g * w;\n            w *= d;",
                               "            bin = bin * d + g;"),
+    "q_exponent_from_p": ("uint64_t cq = or_powmod_native32(mq, eq, q);",
+                          "uint64_t cq = or_powmod_native32(mq, ep, q);"),
+    "unit_skip_rejected": ("a < 1 || a >= Q", "a < 2 || a >= Q"),
+    "crt_exponent_wrong_modulus": ("return ra + a * t;", "return ra + b * t;"),
 }
 
 
