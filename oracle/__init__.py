@@ -83,6 +83,7 @@ def _configure(L):
         "or_crt_encrypt2": (u64, [u64, u64, u64, u64, u64, u64, u64]),
         "or_crt_exponent": (u64, [u64, u64, u64, u64]),
         "or_unit": (dbl, [u64, u64]),
+        "or_unit_exact": (dbl, [u64, u64]),
         "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
         "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
         "or_sample": (i32, [ctypes.c_void_p, pu64, pu64, pu64, u64, pu64, pdbl]),
@@ -262,6 +263,12 @@ def sample_many(p, q, e, a, m, s, ks_list, q_mod=Q):
     if rc != 0:
         raise RuntimeError(f"oracle sample_many failed ({rc})")
     return c, r
+
+
+def unit_exact(c, n) -> float:
+    """RN(c / n) of the exact rational, with the 1.0 guard (the other reading of the
+    division of Eq. CodeFloatingPointStep)."""
+    return lib().or_unit_exact(c, n)
 
 
 def unit_many(c: np.ndarray, n: int) -> np.ndarray:

@@ -29,6 +29,8 @@
  *                                E from a Python CRT, permutation of Z_n
  *   or_unit                      pinned: exact-rational rounding of the two
  *                                IEEE conversions and the division
+ *   or_unit_exact                pinned: Python's correctly rounded
+ *                                float(Fraction(c, n)), ties built exactly
  *   or_generate (sequence)       pinned by the closed form of Eq. pseudoskip
  *                                on tiny Q and by the two routes agreeing
  *   or_params_from_seed          pinned: SplitMix64 published test values
@@ -300,6 +302,40 @@ double or_unit(uint64_t c, uint64_t n)
     volatile double dc = (double)c;
     volatile double dn = (double)n;
     double r = dc / dn;
+    if (r >= 1.0)
+        r = 0x1.fffffffffffffp-1;
+    return r;
+}
+
+/* The other reading of the division: r = RN(c / n), the exact rational c/n
+ * rounded once to the nearest double (ties to even), with the same 1.0
+ * guard. Long division, one bit at a time: the quotient bits of c/n < 1 are
+ * produced until 53 significant bits and the next (round) bit are known; the
+ * remainder left over decides the ties (sticky). */
+double or_unit_exact(uint64_t c, uint64_t n)
+{
+    if (c == 0)
+        return 0.0;
+    u128 rem = c;
+    int pos = 0, nbits = 0;
+    uint64_t sig = 0;
+    while (nbits < 54) {
+        rem <<= 1;
+        pos++;
+        const int b = rem >= n;
+        if (b)
+            rem -= n;
+        if (nbits > 0 || b) {
+            sig = (sig << 1) | (uint64_t)b;
+            nbits++;
+        }
+    }
+    /* sig: 53 significand bits and the round bit (weight 2^-pos) */
+    uint64_t m = sig >> 1;
+    const int round_bit = (int)(sig & 1), sticky = rem != 0;
+    if (round_bit && (sticky || (m & 1)))
+        m++;
+    double r = ldexp((double)m, -(pos - 1));
     if (r >= 1.0)
         r = 0x1.fffffffffffffp-1;
     return r;

@@ -147,3 +147,40 @@ def test_equal_exponents_are_the_ordinary_generator():
     c1, r1, m_b, s_b = oracle.generate(p, q, e, m0, 1, 777, eq=e)
     np.testing.assert_array_equal(c0, c1)
     assert (m_a, s_a) == (m_b, s_b)
+
+
+def _exact_want(c, n):
+    from fractions import Fraction
+
+    w = float(Fraction(c, n))  # Python rounds a Fraction once, to nearest even
+    return 1.0 - 2.0 ** -53 if w >= 1.0 else w
+
+
+def test_exact_rational_division():
+    from fractions import Fraction
+
+    rng = random.Random(8)
+    for seed in range(500, 515):
+        p, q, _, _ = _pq(seed)
+        n = p * q
+        cs = [1, 2, 3, n - 1, n - 2, n // 2, n // 3] + [rng.randrange(n) for _ in range(2000)]
+        # c/n just below and just above the midpoint of two neighbouring doubles
+        for _ in range(300):
+            x = rng.random()
+            mid = (Fraction(x) + Fraction(math.nextafter(x, 1.0))) / 2
+            c = math.floor(mid * n)
+            cs += [c, c + 1]
+        for c in cs:
+            if 0 <= c < n:
+                assert oracle.unit_exact(c, n) == _exact_want(c, n), (c, n)
+
+
+def test_exact_and_paper_readings_differ_often():
+    """The two readings of r = c / n disagree in a large share of draws (why the reading
+    is pinned)."""
+    rng = random.Random(9)
+    p, q, _, _ = _pq(600)
+    n = p * q
+    cs = [rng.randrange(n) for _ in range(20000)]
+    diff = sum(oracle.unit(c, n) != oracle.unit_exact(c, n) for c in cs)
+    assert diff > 0.1 * len(cs)

@@ -193,8 +193,19 @@ def check_modes(L):
     return True
 
 
+def check_unit_exact(L):
+    rng = random.Random(10)
+    for n in (4294967291 * 4294967279, 2147483659 * 2147483693):
+        for c in [1, n - 1, n // 2] + [rng.randrange(n) for _ in range(3000)]:
+            want = float(Fraction(c, n))
+            want = 0.9999999999999999 if want >= 1.0 else want
+            if L.or_unit_exact(c, n) != want:
+                return False
+    return True
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
-          check_rsa, check_unit, check_split, check_histogram, check_modes]
+          check_rsa, check_unit, check_split, check_histogram, check_modes, check_unit_exact]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -204,8 +215,8 @@ MUTANTS = {
                             "            m = or_addmod(m, s % n, n);\n            mp = (mp + s) % p;\n            mq = (mq + s) % q;\n            s = s_direct;"),
     "garner_no_reduction": ("uint64_t diff = (cp + p - (cq % p)) % p;",
                             "uint64_t diff = (cp + p - cq) % p;"),
-    "guard_strict": ("if (r >= 1.0)\n        r = 0x1.fffffffffffffp-1;",
-                     "if (r > 1.0)\n        r = 0x1.fffffffffffffp-1;"),
+    "guard_strict": ("double r = dc / dn;\n    if (r >= 1.0)\n        r = 0x1.fffffffffffffp-1;",
+                     "double r = dc / dn;\n    if (r > 1.0)\n        r = 0x1.fffffffffffffp-1;"),
     "four_mr_bases": ("int bases = (n < ((uint64_t)1 << 32)) ? 5 : 12;",
                       "int bases = (n < ((uint64_t)1 << 32)) ? 4 : 12;"),
     "no_square": ("        b = or_mulmod(b, b, m);\n        e >>= 1;\n    }\n    return r;\n}\n\n/* b^e mod m for m < 2^32",
@@ -221,6 +232,7 @@ MUTANTS = {
                           "uint64_t cq = or_powmod_native32(mq, ep, q);"),
     "unit_skip_rejected": ("a < 1 || a >= Q", "a < 2 || a >= Q"),
     "crt_exponent_wrong_modulus": ("return ra + a * t;", "return ra + b * t;"),
+    "exact_division_truncates": ("    if (round_bit && (sticky || (m & 1)))\n        m++;\n", ""),
 }
 
 
