@@ -49,7 +49,7 @@ extern "C" {
 #define RSAPRNG_ERR_RANGE (-3)       /* p or q outside [2^31, 2^32) */
 #define RSAPRNG_ERR_P_EQ_Q (-4)      /* p == q */
 #define RSAPRNG_ERR_E (-5)           /* e even, < 3, or gcd(e,(p-1)(q-1)) != 1 */
-#define RSAPRNG_ERR_ROOT (-6)        /* a is not one of the allowed roots */
+#define RSAPRNG_ERR_ROOT (-6)        /* a is not an allowed multiplier (or a = 1 split) */
 #define RSAPRNG_ERR_OOM (-7)         /* device or host allocation failed */
 #define RSAPRNG_ERR_BUDGET (-8)      /* request larger than the server budget */
 #define RSAPRNG_ERR_CUDA (-9)        /* a CUDA runtime call failed */
@@ -94,6 +94,13 @@ enum {
 /* Exponent rules for rsaprng_params_from_seed. */
 enum { RSAPRNG_E_SMALLEST = 0, RSAPRNG_E_UNIFORM = 1, RSAPRNG_E_AT_LEAST = 2 };
 
+/* Reading of the division r = c / n (Eq. CodeFloatingPointStep). */
+enum {
+    RSAPRNG_ROUND_DEFAULT = 0, /* = RSAPRNG_ROUND_PAPER */
+    RSAPRNG_ROUND_PAPER = 1,   /* RN(RN(c) / RN(n)): C's (double)c / (double)n */
+    RSAPRNG_ROUND_EXACT = 2    /* RN(c / n) of the exact rational (the other reading) */
+};
+
 /* Tuning knobs; zero fields mean "use the tuned/default value". */
 typedef struct {
     uint32_t struct_size;       /* sizeof(rsaprng_config) */
@@ -108,7 +115,9 @@ typedef struct {
                                    exceeds one resident block's share of the
                                    launch, in whole tiles */
     int32_t require_safe;       /* p, q must be safe primes (Sec. V) */
-    int32_t reserved[7];
+    int32_t rounding;           /* RSAPRNG_ROUND_*; with RSAPRNG_ROUND_EXACT the divide
+                                   route is ignored (one integer route computes it) */
+    int32_t reserved[6];
 } rsaprng_config;
 
 /* ------------------------------------------------------------- context */
@@ -132,8 +141,10 @@ uint64_t rsaprng_instance_count(const rsaprng_ctx *ctx);
  * deterministic Rabin-Miller (Sec. V). Synchronous host->device write. */
 int rsaprng_instance_create(rsaprng_ctx *ctx, uint64_t p, uint64_t q, uint64_t e, uint64_t seed,
                             rsaprng_id *out);
-/* Explicit skip multiplier and start state: a must be an allowed root,
- * m0 < n, 1 <= s0 < Q. */
+/* Explicit skip multiplier and start state: a must be an allowed multiplier
+ * (rsaprng_root_allowed), m0 < n, 1 <= s0 < Q. a = 1 gives the unit skip
+ * (s0 = 1: m_k = m_0 + k mod n, the block cipher in counter mode) or the
+ * constant skip s_k = b = s0 of Sec. IV. */
 int rsaprng_instance_create_ex(rsaprng_ctx *ctx, uint64_t p, uint64_t q, uint64_t e, uint64_t a,
                                uint64_t m0, uint64_t s0, rsaprng_id *out);
 /* `count` instances from host arrays (same rules as rsaprng_instance_create);
@@ -148,10 +159,28 @@ int rsaprng_instances_create_seeded(rsaprng_ctx *ctx, uint64_t count, const uint
                                     int e_rule, uint64_t e_lo, uint64_t e_hi,
                                     rsaprng_id *out_first);
 
+/* CRT exponents (the paper's note on large exponents, Sec. V): the p residue
+ * is raised to e_p and the q residue to e_q, c = CRT(m_p^e_p mod p,
+ * m_q^e_q mod q) by Garner's formula. e_p, e_q odd in [3, 2^32) with
+ * gcd(e_p, p - 1) = gcd(e_q, q - 1) = 1. When e_p = e_q (mod gcd(p-1, q-1))
+ * the output is m^e mod n for the large exponent e = e_p (mod p - 1),
+ * e = e_q (mod q - 1); otherwise it is still a permutation of Z_n. Other
+ * arguments as rsaprng_instance_create_ex. Such an instance runs on the CRT
+ * route only: a launch with RSAPRNG_MODEXP_MONT64 that includes it fails
+ * with RSAPRNG_ERR_ARG. Errors: RSAPRNG_ERR_RANGE, _P_EQ_Q, _NOT_PRIME, _E,
+ * _ROOT, _STATE. */
+int rsaprng_instance_create_crt(rsaprng_ctx *ctx, uint64_t p, uint64_t q, uint64_t e_p,
+                                uint64_t e_q, uint64_t a, uint64_t m0, uint64_t s0,
+                                rsaprng_id *out);
+/* The exponents of the p and q residues (equal unless created by
+ * rsaprng_instance_create_crt). */
+int rsaprng_get_exponents(const rsaprng_ctx *ctx, rsaprng_id id, uint64_t *e_p, uint64_t *e_q);
+
 /* Stream splitting (Sec. VI): Mv children of `parent`, child gamma with the
  * parent's parameters and current message, and skip
  *     s^(gamma) = s * a^(gamma floor((Q-1)/Mv)) mod Q.
- * Child 0 continues the parent's stream. The parent is unchanged. */
+ * Child 0 continues the parent's stream. The parent is unchanged. A constant
+ * skip (a = 1) has no jump-ahead: RSAPRNG_ERR_ROOT. */
 int rsaprng_split(rsaprng_ctx *ctx, rsaprng_id parent, uint32_t Mv, rsaprng_id *out_children);
 
 /* Checkpoint / resume (Sec. IV: the state is {m, s}). Synchronous. */
@@ -334,8 +363,9 @@ int rsaprng_is_prime(uint64_t x);
 int rsaprng_validate_params(uint64_t p, uint64_t q, uint64_t e, int require_safe);
 /* 1 if a is allowed as a skip multiplier: the recommended root, the eight
  * listed roots of Sezgin & Sezgin that are primitive (3163786287 is not: it
- * is a quadratic residue mod Q), or one of the five smallest primitive roots
- * {3, 6, 7, 10, 11} used for the weakened-generator tests (Sec. VII). */
+ * is a quadratic residue mod Q), one of the five smallest primitive roots
+ * {3, 6, 7, 10, 11} used for the weakened-generator tests (Sec. VII), or 1
+ * (the unit / constant skip of Sec. IV). */
 int rsaprng_root_allowed(uint64_t a);
 
 /* Instance parameters from one 64-bit seed (the rule the workloads use; it
@@ -351,7 +381,8 @@ int rsaprng_params_from_seed(uint64_t seed, int e_rule, uint64_t e_lo, uint64_t 
 
 /* The output step alone (Eq. CodeFloatingPointStep with the Sec. V guard):
  * d_r[k] = RN(RN(d_c[k]) / RN(n_id)), 1 - 2^-53 in place of 1.0, for k < N,
- * using division route `divide` (RSAPRNG_DIVIDE_*; AUTO = the context's).
+ * using division route `divide` (RSAPRNG_DIVIDE_*; AUTO = the context's);
+ * RN(d_c[k] / n_id) when the context's rounding is RSAPRNG_ROUND_EXACT.
  * d_c values must be < n of instance `id`. Asynchronous on `stream`. */
 int rsaprng_unit_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, const uint64_t *d_c,
                      double *d_r, int divide, void *stream);

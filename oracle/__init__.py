@@ -90,6 +90,7 @@ def _configure(L):
         "or_sample_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64,
                                  pu64, pu64, pu64, pdbl]),
         "or_unit_many": (None, [pu64, u64, pdbl, u64]),
+        "or_unit_exact_many": (None, [pu64, u64, pdbl, u64]),
         "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
                                    pu64, pu64, pu64, pdbl, i32]),
         "or_max_threads": (i32, []),
@@ -269,6 +270,13 @@ def unit_exact(c, n) -> float:
     """RN(c / n) of the exact rational, with the 1.0 guard (the other reading of the
     division of Eq. CodeFloatingPointStep)."""
     return lib().or_unit_exact(c, n)
+
+
+def unit_exact_many(c: np.ndarray, n: int) -> np.ndarray:
+    c = np.ascontiguousarray(c, dtype=np.uint64)
+    r = np.empty(len(c), np.float64)
+    lib().or_unit_exact_many(_p64(c), n, _pd(r), len(c))
+    return r
 
 
 def unit_many(c: np.ndarray, n: int) -> np.ndarray:

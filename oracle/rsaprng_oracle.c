@@ -494,6 +494,13 @@ int or_sample_many(uint64_t count, const uint64_t *p, const uint64_t *q, const u
     return err;
 }
 
+/* r[i] = or_unit_exact(c[i], n) for i < count. */
+void or_unit_exact_many(const uint64_t *c, uint64_t n, double *r, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; i++)
+        r[i] = or_unit_exact(c[i], n);
+}
+
 /* r[i] = or_unit(c[i], n) for i < count. */
 void or_unit_many(const uint64_t *c, uint64_t n, double *r, uint64_t count)
 {

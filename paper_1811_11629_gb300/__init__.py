@@ -157,6 +157,19 @@ class Context:
               "instance_create_ex")
         return out.value
 
+    def create_crt(self, p, q, e_p, e_q, a, m0, s0) -> int:
+        """Instance with CRT exponents e_p (p residue) and e_q (q residue)."""
+        out = ctypes.c_uint32()
+        check(self.L.rsaprng_instance_create_crt(self.h, p, q, e_p, e_q, a, m0, s0,
+                                                 ctypes.byref(out)), "instance_create_crt")
+        return out.value
+
+    def exponents(self, id_: int):
+        ep, eq = ctypes.c_uint64(), ctypes.c_uint64()
+        check(self.L.rsaprng_get_exponents(self.h, id_, ctypes.byref(ep), ctypes.byref(eq)),
+              "get_exponents")
+        return ep.value, eq.value
+
     def create_bulk(self, p, q, e, seed) -> int:
         p, q, e, seed = (np.ascontiguousarray(x, dtype=np.uint64) for x in (p, q, e, seed))
         out = ctypes.c_uint32()

@@ -25,6 +25,7 @@ MODEXP_AUTO, MODEXP_CRT32, MODEXP_MONT64 = 0, 1, 2
 DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_RECIP = 0, 1, 2, 3, 4
 E_SMALLEST, E_UNIFORM, E_AT_LEAST = 0, 1, 2
 HIST_HIGH, HIST_LOW = 0, 1
+ROUND_DEFAULT, ROUND_PAPER, ROUND_EXACT = 0, 1, 2
 Q = (1 << 63) - 25
 DEFAULT_ROOT = 2307085864
 
@@ -40,7 +41,8 @@ CODES = {v: k for k, v in ERRORS.items()}
 class Config(ctypes.Structure):
     _fields_ = [("struct_size", u32), ("modexp", i32), ("divide", i32),
                 ("threads_per_block", i32), ("numbers_per_thread", i32), ("blocks_per_sm", i32),
-                ("chunk", u64), ("require_safe", i32), ("reserved", i32 * 7)]
+                ("chunk", u64), ("require_safe", i32), ("rounding", i32),
+                ("reserved", i32 * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -72,6 +74,8 @@ SIGNATURES = {
     "rsaprng_generate_batch": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_generate_batch_host": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_histogram": (i32, [vp, u64, pu32, pu64, u32, u32, i32, vp, vp]),
+    "rsaprng_instance_create_crt": (i32, [vp, u64, u64, u64, u64, u64, u64, u64, pu32]),
+    "rsaprng_get_exponents": (i32, [vp, u32, pu64, pu64]),
     "rsaprng_chi2_uniform": (i32, [pu64, u64, pdbl, pu64]),
     "rsaprng_plan_create": (i32, [vp, u64, pu32, pu64, pu64, pvp]),
     "rsaprng_plan_launch": (i32, [vp, vp, vp, vp]),

@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 static const rsaprng_config kDefaultConfig = {
     sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP, 128, 16, 0, 1ULL << 18, 0,
-    {0, 0, 0, 0, 0, 0, 0}};
+    RSAPRNG_ROUND_DEFAULT, {0, 0, 0, 0, 0, 0}};
 
 static int check_config(const rsaprng_config &c)
 {
@@ -54,6 +54,8 @@ static int check_config(const rsaprng_config &c)
         return fail(RSAPRNG_ERR_ARG, "config: numbers_per_thread must be 2, 4, 8 or 16");
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32)
         return fail(RSAPRNG_ERR_ARG, "config: blocks_per_sm out of range");
+    if (c.rounding < 0 || c.rounding > RSAPRNG_ROUND_EXACT)
+        return fail(RSAPRNG_ERR_ARG, "config: rounding out of range");
     return RSAPRNG_OK;
 }
 
@@ -75,6 +77,8 @@ static rsaprng_config merged(const rsaprng_config &base, const rsaprng_config *o
     if (over->chunk)
         c.chunk = over->chunk;
     c.require_safe = over->require_safe;
+    if (over->rounding)
+        c.rounding = over->rounding;
     return c;
 }
 
@@ -98,7 +102,8 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
     if (g.modexp == MODEXP_MONT64 && g.L > 8)
         g.L = 8;  // the 64-bit route has no 16-output tiling (register budget)
-    g.divide = cfg.divide == RSAPRNG_DIVIDE_FP64     ? DIVIDE_FP64
+    g.divide = cfg.rounding == RSAPRNG_ROUND_EXACT   ? DIVIDE_EXACT
+               : cfg.divide == RSAPRNG_DIVIDE_FP64   ? DIVIDE_FP64
                : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
                : cfg.divide == RSAPRNG_DIVIDE_RECIP  ? DIVIDE_RECIP
                                                      : DIVIDE_INT;
@@ -166,7 +171,12 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
             return fail(RSAPRNG_ERR_ID, "request %llu: unknown instance id %u",
                         (unsigned long long)i, ids[i]);
         order[i] = i;
-        work += counts[i] * cost_per_number(c->h_params[ids[i]].e);
+        const InstParams &P = c->h_params[ids[i]];
+        work += counts[i] * cost_per_number(std::max(P.e, P.eq));
+        if (P.e != P.eq && cfg.modexp == RSAPRNG_MODEXP_MONT64)
+            return fail(RSAPRNG_ERR_ARG,
+                        "instance %u has CRT exponents; the 64-bit route needs one exponent",
+                        ids[i]);
     }
     // Cost of one piece: the work spread over the resident blocks of the
     // launch, kPiecesPerBlock pieces each; pieces are whole tiles.
@@ -188,7 +198,7 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
         while (g1 < nreq && ids[order[g1]] == id)
             g1++;
         pieces.clear();
-        const uint64_t w = cost_per_number(c->h_params[id].e);
+        const uint64_t w = cost_per_number(std::max(c->h_params[id].e, c->h_params[id].eq));
         uint64_t total = 0;
         for (uint64_t k = g0; k < g1; k++)
             total += counts[order[k]];
@@ -452,7 +462,7 @@ const char *rsaprng_strerror(int code)
     case RSAPRNG_ERR_RANGE: return "p or q outside [2^31, 2^32)";
     case RSAPRNG_ERR_P_EQ_Q: return "p equals q";
     case RSAPRNG_ERR_E: return "invalid exponent e";
-    case RSAPRNG_ERR_ROOT: return "skip multiplier is not an allowed primitive root";
+    case RSAPRNG_ERR_ROOT: return "skip multiplier not allowed (or a constant skip split)";
     case RSAPRNG_ERR_OOM: return "out of memory";
     case RSAPRNG_ERR_BUDGET: return "request exceeds the output budget";
     case RSAPRNG_ERR_CUDA: return "CUDA error";
@@ -650,6 +660,37 @@ int rsaprng_instance_create_ex(rsaprng_ctx *c, uint64_t p, uint64_t q, uint64_t 
     return append_instances(c, ps, {m0}, {s0}, out);
 }
 
+int rsaprng_instance_create_crt(rsaprng_ctx *c, uint64_t p, uint64_t q, uint64_t e_p,
+                                uint64_t e_q, uint64_t a, uint64_t m0, uint64_t s0,
+                                rsaprng_id *out)
+{
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null ctx");
+    int rc = validate_crt_exponents(p, q, e_p, e_q, c->cfg.require_safe != 0);
+    if (rc)
+        return fail(rc, "instance (p=%llu, q=%llu, e_p=%llu, e_q=%llu): %s",
+                    (unsigned long long)p, (unsigned long long)q, (unsigned long long)e_p,
+                    (unsigned long long)e_q, rsaprng_strerror(rc));
+    if (root_index(a) < 0)
+        return fail(RSAPRNG_ERR_ROOT, "a=%llu is not an allowed multiplier", (unsigned long long)a);
+    if (m0 >= p * q || s0 == 0 || s0 >= kQ)
+        return fail(RSAPRNG_ERR_STATE, "start state out of range");
+    std::vector<InstParams> ps(1);
+    make_params(p, q, e_p, a, ps[0], e_q);
+    return append_instances(c, ps, {m0}, {s0}, out);
+}
+
+int rsaprng_get_exponents(const rsaprng_ctx *c, rsaprng_id id, uint64_t *e_p, uint64_t *e_q)
+{
+    if (!c || !e_p || !e_q)
+        return fail(RSAPRNG_ERR_ARG, "get_exponents: null argument");
+    if (id >= c->count)
+        return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
+    *e_p = c->h_params[id].e;
+    *e_q = c->h_params[id].eq;
+    return RSAPRNG_OK;
+}
+
 int rsaprng_instance_create(rsaprng_ctx *c, uint64_t p, uint64_t q, uint64_t e, uint64_t seed,
                             rsaprng_id *out)
 {
@@ -762,6 +803,8 @@ int rsaprng_split(rsaprng_ctx *c, rsaprng_id parent, uint32_t Mv, rsaprng_id *ou
     if (rc)
         return rc;
     const InstParams P = c->h_params[parent];
+    if (P.a == 1)
+        return fail(RSAPRNG_ERR_ROOT, "split: a constant skip (a = 1) has no jump-ahead");
     const uint64_t stride = (kQ - 1) / Mv;
     const uint64_t a_stride = powQ(P.a, stride);
     std::vector<InstParams> ps(Mv, P);
@@ -930,9 +973,10 @@ int rsaprng_unit_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, const uint64_t *
         divide = c->cfg.divide;
     cudaSetDevice(c->device);
     cudaError_t e = launch_unit(ctx_tables(c), id, N, d_c, d_r,
-                                divide == RSAPRNG_DIVIDE_INT    ? DIVIDE_INT
-                                : divide == RSAPRNG_DIVIDE_FP64 ? DIVIDE_FP64
-                                                                : DIVIDE_RECIP,
+                                c->cfg.rounding == RSAPRNG_ROUND_EXACT ? DIVIDE_EXACT
+                                : divide == RSAPRNG_DIVIDE_INT         ? DIVIDE_INT
+                                : divide == RSAPRNG_DIVIDE_FP64        ? DIVIDE_FP64
+                                                                       : DIVIDE_RECIP,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "unit launch");

@@ -62,8 +62,8 @@ struct rsaprng_ctx {
     int next_slot = 0;
     uint64_t launches = 0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device bytes moved by the library
-    int occ_cache[4][4][2][4];  // blocks/SM by (threads 64/128/256/512, L index, modexp, divide)
-    size_t occ_smem[4][4][2][4];
+    int occ_cache[4][4][2][5];  // blocks/SM by (threads 64/128/256/512, L index, modexp, divide)
+    size_t occ_smem[4][4][2][5];
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
 };

@@ -182,7 +182,7 @@ cudaError_t launch_hist_t(const GenLaunch &g, const DeviceTables &t, const WorkI
 
 // The float digits need r itself, which every division route gives bit for
 // bit: the integer route and the reciprocal route are instantiated, and the
-// other two map to the reciprocal one.
+// other two map to the reciprocal one; the exact-rational reading has its own.
 template <int DIV>
 const void *hist_kernel_ptr_l(int L, int modexp)
 {
@@ -208,6 +208,8 @@ const void *hist_kernel_ptr_l(int L, int modexp)
 
 const void *hist_kernel_ptr(const GenLaunch &g)
 {
+    if (g.divide == DIVIDE_EXACT)
+        return hist_kernel_ptr_l<DIVIDE_EXACT>(g.L, g.modexp);
     return g.divide == DIVIDE_INT ? hist_kernel_ptr_l<DIVIDE_INT>(g.L, g.modexp)
                                   : hist_kernel_ptr_l<DIVIDE_RECIP>(g.L, g.modexp);
 }
@@ -239,6 +241,8 @@ cudaError_t launch_histogram(const GenLaunch &g, const DeviceTables &t, const Wo
                              uint32_t nitems, uint32_t *ticket, const HistArgs &h,
                              cudaStream_t stream)
 {
+    if (g.divide == DIVIDE_EXACT)
+        return launch_hist_div<DIVIDE_EXACT>(g, t, items, nitems, ticket, h, stream);
     if (g.divide == DIVIDE_INT)
         return launch_hist_div<DIVIDE_INT>(g, t, items, nitems, ticket, h, stream);
     return launch_hist_div<DIVIDE_RECIP>(g, t, items, nitems, ticket, h, stream);

@@ -115,19 +115,27 @@ __device__ __forceinline__ u64 mont64(u64 a, u64 b, u64 n, u64 ninv)
 // m_j may be any 64-bit representative of the message's class mod n: the
 // chain values stay below 2^32 and congruent, and the final product with
 // kp < p (kq < q) returns the fully reduced residue.
+// With CRT exponents (the q residue raised to eq != e, the paper's note on
+// large exponents in Sec. V) both residues run in the same loop over the bits
+// of the longer exponent: the residue whose exponent is shorter starts from
+// the Montgomery form of 1 (2^32 mod p = 2^32 - p, below p as p > 2^31),
+// which squaring leaves unchanged, so at its own top bit it becomes REDC(m)
+// exactly as the ordinary chain starts; each residue multiplies on its own
+// exponent's bits.
 template <int L>
 __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
 {
-    const u32 p = P.p, q = P.q, pinv = P.pinv, qinv = P.qinv, e = P.e;
+    const u32 p = P.p, q = P.q, pinv = P.pinv, qinv = P.qinv, e = P.e, eq = P.eq;
+    const int top = 31 - __clz(e | eq);
+    const bool p_on = (e >> top) & 1, q_on = (eq >> top) & 1;
     u32 yp[L], yq[L], zp[L], zq[L];
 #pragma unroll
     for (int j = 0; j < L; j++) {
         yp[j] = redc32(m[j], p, pinv);
         yq[j] = redc32(m[j], q, qinv);
-        zp[j] = yp[j];
-        zq[j] = yq[j];
+        zp[j] = p_on ? yp[j] : 0u - p;
+        zq[j] = q_on ? yq[j] : 0u - q;
     }
-    const int top = 31 - __clz(e);
     for (int bit = top - 1; bit >= 0; bit--) {
         u64 Tp[L], Tq[L];
 #pragma unroll
@@ -140,7 +148,8 @@ __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], cons
             zp[j] = redc32(Tp[j], p, pinv);
             zq[j] = redc32(Tq[j], q, qinv);
         }
-        if ((e >> bit) & 1) {
+        const bool mp = (e >> bit) & 1, mq = (eq >> bit) & 1;
+        if (mp && mq) {
 #pragma unroll
             for (int j = 0; j < L; j++) {
                 Tp[j] = (u64)zp[j] * yp[j];
@@ -151,6 +160,14 @@ __device__ __forceinline__ void encrypt_crt(const u64 (&m)[L], u64 (&c)[L], cons
                 zp[j] = redc32(Tp[j], p, pinv);
                 zq[j] = redc32(Tq[j], q, qinv);
             }
+        } else if (mp) {
+#pragma unroll
+            for (int j = 0; j < L; j++)
+                zp[j] = mont32(zp[j], yp[j], p, pinv);
+        } else if (mq) {
+#pragma unroll
+            for (int j = 0; j < L; j++)
+                zq[j] = mont32(zq[j], yq[j], q, qinv);
         }
     }
 #pragma unroll
@@ -227,6 +244,72 @@ __device__ __forceinline__ double unit_recip(u64 c, double dn, double y)
     return guard_below_one(__fma_rn(r, y, q0));
 }
 
+// 2/1 division by an invariant normalised divisor (Moller & Granlund,
+// "Improved division by invariant integers", IEEE TC 2011, Algorithm 4):
+// (u1 2^64 + u0) = q d + r for d >= 2^63, u1 < d and v = floor((2^128 - 1) /
+// d) - 2^64.
+__device__ __forceinline__ void div21(u64 u1, u64 u0, u64 d, u64 v, u64 &q, u64 &r)
+{
+    u64 q0 = v * u1;
+    u64 q1 = __umul64hi(v, u1);
+    q0 += u0;
+    q1 += u1 + (q0 < u0 ? 1 : 0);
+    q1 += 1;
+    r = u0 - q1 * d;
+    if (r > q0) {
+        q1 -= 1;
+        r += d;
+    }
+    if (r >= d) {
+        q1 += 1;
+        r -= d;
+    }
+    q = q1;
+}
+
+// The other reading of the division: r = RN(c / n) of the exact rational,
+// with the same 1.0 guard. With N = n 2^s normalised (s = nsh) and C = c 2^s
+// < N, the quotient digits of c/n in base 2^64 come from 2/1 divisions by N:
+// (C, 0) / N = q1 rem r1, (r1, 0) / N = q2 rem r2, and c/n = (q1 2^64 + q2 +
+// r2 / N) 2^-128. With lz leading zeros in q1 (q1 >= 1 since c/n > 2^-64),
+// the significand is the 53 bits of (q1, q2) below bit 127 - lz; the bits
+// under it and the remainder decide the rounding (ties to even). The second
+// division is needed only when q1 alone holds fewer than 54 bits (lz > 10).
+__device__ __forceinline__ double unit_exact(u64 c, const InstParams &P)
+{
+    if (c == 0)
+        return 0.0;
+    const u64 N = P.n << P.nsh, C = c << P.nsh;
+    u64 q1, r1;
+    div21(C, 0, N, P.vn, q1, r1);
+    const int lz = __clzll(q1);
+    u64 sig, rem, half;
+    bool sticky;
+    if (lz <= 10) {
+        const int sh = 11 - lz;  // bits of q1 under the significand
+        sig = q1 >> sh;
+        rem = q1 & ((1ULL << sh) - 1);
+        half = 1ULL << (sh - 1);
+        sticky = r1 != 0;
+    } else {
+        u64 q2, r2;
+        div21(r1, 0, N, P.vn, q2, r2);
+        const int sh = 75 - lz;  // in [12, 64]: bits of q2 under the significand
+        sig = (q1 << (64 - sh)) | (sh == 64 ? 0 : (q2 >> sh));
+        rem = sh == 64 ? q2 : (q2 & ((1ULL << sh) - 1));
+        half = 1ULL << (sh - 1);
+        sticky = r2 != 0;
+    }
+    if (rem > half || (rem == half && (sticky || (sig & 1))))
+        sig++;
+    // value sig 2^(-53 - lz); sig in [2^52, 2^53], a rounded-up 2^53 carries
+    // into the exponent field
+    u64 bits = ((u64)(1021 - lz) << 52) + sig;
+    if (bits > ONE_MINUS_ULP_BITS)
+        bits = ONE_MINUS_ULP_BITS;
+    return __longlong_as_double((long long)bits);
+}
+
 // The same value from integers only. RN(c) = Mc 2^Ec is rounded to 53 bits
 // with ties to even; RN(n) = Mn 2^En is a per-instance constant. The
 // significand quotient X / Mn with X = Mc 2^52 (Mc >= Mn) or Mc 2^53
@@ -271,21 +354,8 @@ __device__ __forceinline__ double unit_int(u64 c, const InstParams &P)
         u0 = 0;
         E = ec - P.en - 1;
     }
-    // (q1, q0) = v u1 + (u1, u0)
-    u64 q0 = v * u1;
-    u64 q1 = __umul64hi(v, u1);
-    q0 += u0;
-    q1 += u1 + (q0 < u0 ? 1 : 0);
-    q1 += 1;
-    u64 r = u0 - q1 * d;
-    if (r > q0) {
-        q1 -= 1;
-        r += d;
-    }
-    if (r >= d) {
-        q1 += 1;
-        r -= d;
-    }
+    u64 q1, r;
+    div21(u1, u0, d, v, q1, r);
     const u64 halfd = d >> 1;
     if (r > halfd || (r == halfd && (q1 & 1)))
         q1++;

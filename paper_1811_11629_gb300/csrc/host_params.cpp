@@ -9,12 +9,14 @@ namespace rsaprng {
 
 // Root list: the L'Ecuyer-Blouin-Couture recommendation, the eight Sezgin &
 // Sezgin multipliers that are primitive roots mod Q (3163786287 from the same
-// list is a quadratic residue and is left out), and the five smallest
-// primitive roots mod Q (Sec. VII's weakened-generator tests).
+// list is a quadratic residue and is left out), the five smallest primitive
+// roots mod Q (Sec. VII's weakened-generator tests), and 1: with a = 1 the
+// skip stays s_0, the unit (s_0 = 1) or constant skip of Sec. IV.
 const u64 kRoots[kNumRoots] = {
     2307085864ULL, 3157107955ULL, 3200261722ULL, 3211103532ULL, 3338736601ULL,
     3423977237ULL, 3465965455ULL, 3474009732ULL, 3512424704ULL,
     3ULL,          6ULL,          7ULL,          10ULL,         11ULL,
+    1ULL,
 };
 
 int root_index(u64 a)
@@ -136,7 +138,7 @@ u64 splitmix64_next(u64 &state)
     return z ^ (z >> 31);
 }
 
-int validate_pqe(u64 p, u64 q, u64 e, bool require_safe)
+int validate_pq(u64 p, u64 q, bool require_safe)
 {
     const u64 lo = 1ULL << 31, hi = 1ULL << 32;
     if (p < lo || p >= hi || q < lo || q >= hi)
@@ -147,15 +149,36 @@ int validate_pqe(u64 p, u64 q, u64 e, bool require_safe)
         return RSAPRNG_ERR_NOT_PRIME;
     if (require_safe && (!is_prime((p - 1) / 2) || !is_prime((q - 1) / 2)))
         return RSAPRNG_ERR_NOT_PRIME;
-    if (e < 3 || (e & 1) == 0 || e >= (1ULL << 32))
-        return RSAPRNG_ERR_E;
-    if (gcd64(e, (p - 1) * (q - 1)) != 1)
+    return RSAPRNG_OK;
+}
+
+static bool small_odd_exponent(u64 e) { return e >= 3 && (e & 1) && e < (1ULL << 32); }
+
+int validate_pqe(u64 p, u64 q, u64 e, bool require_safe)
+{
+    const int rc = validate_pq(p, q, require_safe);
+    if (rc)
+        return rc;
+    if (!small_odd_exponent(e) || gcd64(e, (p - 1) * (q - 1)) != 1)
         return RSAPRNG_ERR_E;
     return RSAPRNG_OK;
 }
 
-void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
+int validate_crt_exponents(u64 p, u64 q, u64 ep, u64 eq, bool require_safe)
 {
+    const int rc = validate_pq(p, q, require_safe);
+    if (rc)
+        return rc;
+    if (!small_odd_exponent(ep) || !small_odd_exponent(eq) || gcd64(ep, p - 1) != 1 ||
+        gcd64(eq, q - 1) != 1)
+        return RSAPRNG_ERR_E;
+    return RSAPRNG_OK;
+}
+
+void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o, u64 eq)
+{
+    if (eq == 0)
+        eq = e;
     o = InstParams{};
     const u64 n = p * q;
     o.n = n;
@@ -172,9 +195,10 @@ void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
     // CRT route: the residue entering the chain is REDC(m) = m R^-1 (R = 2^32),
     // the chain ends at m^e R^(1-2e); the product with R^(2e) gives m^e.
     o.kp = (u32)powmod((1ULL << 32) % p, 2 * e, p);
-    o.kq = (u32)powmod((1ULL << 32) % q, 2 * e, q);
+    o.kq = (u32)powmod((1ULL << 32) % q, 2 * eq, q);
     o.garner = (u32)mulmod(invmod(q % p, p), (1ULL << 32) % p, p);
     o.e = (u32)e;
+    o.eq = (u32)eq;
     o.a = (u32)a;
     o.root = (u32)root_index(a);
     // RN(n): n has 63 or 64 significant bits; round to 53 with ties to even.
@@ -203,6 +227,8 @@ void make_params(u64 p, u64 q, u64 e, u64 a, InstParams &o)
     }
     const u128 all = ~(u128)0;
     o.dv = (u64)(all / o.dnorm - ((u128)1 << 64));
+    o.nsh = (u32)__builtin_clzll(n);
+    o.vn = (u64)(all / (u128)(n << o.nsh) - ((u128)1 << 64));
 }
 
 int params_from_seed(u64 seed, int e_rule, u64 e_lo, u64 e_hi, u64 &p, u64 &q, u64 &e,

@@ -275,6 +275,13 @@ const void *select_kernel(int L, int modexp, int divide)
     RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_RECIP)
     RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_RECIP)
     RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_SEL(16, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_SEL(2, MODEXP_MONT64, DIVIDE_EXACT)
+    RSAPRNG_SEL(4, MODEXP_MONT64, DIVIDE_EXACT)
+    RSAPRNG_SEL(8, MODEXP_MONT64, DIVIDE_EXACT)
 #undef RSAPRNG_SEL
     return nullptr;
 }
@@ -440,6 +447,13 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
     RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_RECIP)
     RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_RECIP)
     RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_DISPATCH(2, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(4, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(8, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(16, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(2, MODEXP_MONT64, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(4, MODEXP_MONT64, DIVIDE_EXACT)
+    RSAPRNG_DISPATCH(8, MODEXP_MONT64, DIVIDE_EXACT)
 #undef RSAPRNG_DISPATCH
     return cudaErrorInvalidValue;
 }
@@ -485,7 +499,9 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
     if (N == 0)
         return cudaSuccess;
     const int grid = num_sms() * 8;
-    if (divide == DIVIDE_FP64)
+    if (divide == DIVIDE_EXACT)
+        k_unit<DIVIDE_EXACT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
+    else if (divide == DIVIDE_FP64)
         k_unit<DIVIDE_FP64><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     else if (divide == DIVIDE_RECIP || divide == DIVIDE_HYBRID)
         k_unit<DIVIDE_RECIP><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);

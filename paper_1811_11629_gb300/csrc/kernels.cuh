@@ -53,7 +53,9 @@ enum Modexp { MODEXP_CRT32 = 1, MODEXP_MONT64 = 2 };
 // DIVIDE_HYBRID sends three of every four outputs of a thread through the
 // FP64 pipe and the fourth through the integer pipes; DIVIDE_RECIP uses the
 // reciprocal-and-correction sequence on the FP64 pipe (identical results).
-enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2, DIVIDE_HYBRID = 3, DIVIDE_RECIP = 4 };
+// DIVIDE_EXACT computes the other reading of the division, RN(c / n) of the
+// exact rational (selected by the rounding knob, not by the divide route).
+enum Divide { DIVIDE_INT = 1, DIVIDE_FP64 = 2, DIVIDE_HYBRID = 3, DIVIDE_RECIP = 4, DIVIDE_EXACT = 5 };
 
 struct DeviceTables {
     const InstParams *params;

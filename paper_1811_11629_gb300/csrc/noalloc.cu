@@ -102,6 +102,8 @@ int rsaprng_generate_f64_noalloc(rsaprng_ctx *c, rsaprng_id id, uint64_t N, doub
         return RSAPRNG_ERR_ID;
     if (N > (uint64_t)kNoAllocMaxChunks * kNoAllocMaxChunkLen)
         return RSAPRNG_ERR_ARG;
+    if (c->cfg.modexp == RSAPRNG_MODEXP_MONT64 && c->h_params[id].e != c->h_params[id].eq)
+        return RSAPRNG_ERR_ARG;  // CRT exponents need the CRT route
     if (N == 0)
         return RSAPRNG_OK;
     if (c->device < 0 || c->device >= kMaxDevices)

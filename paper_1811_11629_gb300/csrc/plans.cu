@@ -359,7 +359,14 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
                               {RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP},
                               {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_INT},
                               {RSAPRNG_MODEXP_MONT64, RSAPRNG_DIVIDE_HYBRID}};
+    // Instances with CRT exponents run only on the CRT route.
+    bool one_exponent = true;
+    for (uint64_t i = 0; i < nreq; i++)
+        if (ids[i] < c->count && c->h_params[ids[i]].e != c->h_params[ids[i]].eq)
+            one_exponent = false;
     for (auto &rt : routes) {
+        if (rt[0] == RSAPRNG_MODEXP_MONT64 && !one_exponent)
+            continue;
         rsaprng_config cfg = c->cfg;
         if (rt[0] == RSAPRNG_MODEXP_MONT64 && cfg.numbers_per_thread == 16)
             cfg.numbers_per_thread = 8;

@@ -83,6 +83,8 @@ __device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
         return dev::unit_fp64(c, P.dn);
     else if constexpr (DIV == DIVIDE_RECIP)
         return dev::unit_recip(c, P.dn, P.recip);
+    else if constexpr (DIV == DIVIDE_EXACT)
+        return dev::unit_exact(c, P);
     else
         return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_recip(c, P.dn, P.recip);
 }

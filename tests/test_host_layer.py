@@ -67,7 +67,8 @@ def test_allowed_roots(R):
               3465965455, 3474009732, 3512424704, 3, 6, 7, 10, 11]
     for a in listed:
         assert R.root_allowed(a)
-    for a in [3163786287, 2, 4, 5, 12, 2307085865, 0, 1]:
+    assert R.root_allowed(1)  # the unit / constant skip of Sec. IV
+    for a in [3163786287, 2, 4, 5, 12, 2307085865, 0]:
         assert not R.root_allowed(a)
 
 
