@@ -94,6 +94,8 @@ def _configure(L):
         "or_generate_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64,
                                    pu64, pu64, pu64, pdbl, i32]),
         "or_max_threads": (i32, []),
+        "or_generate_vector": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, u64, pu64,
+                                     pdbl]),
         "or_digit_of_unit": (u64, [dbl, u64]),
         "or_histogram": (i32, [ctypes.c_void_p, pu64, pu64, u64, u64, u64, i32, i32, pu64]),
         "or_histogram_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64, u64,
@@ -328,6 +330,22 @@ def histogram_many(p, q, e, a, m, s, counts, D, d, source=0, route=ROUTE_PAPER, 
     if rc != 0:
         raise RuntimeError(f"oracle histogram_many failed ({rc})")
     return hist
+
+
+def generate_vector(p, q, e, a, m, s, N, q_mod=Q):
+    """The vectorised call of Sec. VI (Eq. vectorize): N steps of the Mv-vector update;
+    returns (c, r) of length N * Mv in k-major order (element gamma of step k at
+    k * Mv + gamma). m, s are advanced in place."""
+    p, q, e, a = (np.ascontiguousarray(x, dtype=np.uint64) for x in (p, q, e, a))
+    assert m.dtype == np.uint64 and s.dtype == np.uint64
+    Mv = len(p)
+    c = np.empty(N * Mv, np.uint64)
+    r = np.empty(N * Mv, np.float64)
+    rc = lib().or_generate_vector(Mv, _p64(p), _p64(q), _p64(e), _p64(a), q_mod, _p64(m), _p64(s),
+                                  N, _p64(c), _pd(r))
+    if rc != 0:
+        raise RuntimeError(f"oracle generate_vector failed ({rc})")
+    return c, r
 
 
 def max_threads() -> int:

@@ -35,6 +35,8 @@
  *                                on tiny Q and by the two routes agreeing
  *   or_params_from_seed          pinned: SplitMix64 published test values
  *                                and the parameter rules re-checked by MR
+ *   or_generate_vector           pinned: equals the per-instance streams of
+ *                                or_generate interleaved k-major
  *   or_digit_of_unit             pinned: exact-rational floor(r d) for
  *                                power-of-two and decimal d, boundaries
  *   or_histogram                 pinned: tuple counts rebuilt from the
@@ -635,6 +637,35 @@ int or_histogram_many(uint64_t count, const uint64_t *p, const uint64_t *q, cons
         }
     }
     return err;
+}
+
+/*
+ * The vectorised call of Sec. VI (Eq. vectorize), written out: the Mv
+ * instances' skips, messages, ciphertexts and reals are updated together, one
+ * vector per step, and step k (k = 1..N) writes element gamma of its vector at
+ * (k - 1) Mv + gamma of c_out / r_out (either may be NULL). Instance gamma has
+ * parameters (p, q, e, a)[gamma] and state (m, s)[gamma], advanced in place.
+ */
+int or_generate_vector(uint64_t Mv, const uint64_t *p, const uint64_t *q, const uint64_t *e,
+                       const uint64_t *a, uint64_t Q, uint64_t *m, uint64_t *s, uint64_t N,
+                       uint64_t *c_out, double *r_out)
+{
+    for (uint64_t k = 0; k < N; k++) {
+        for (uint64_t g = 0; g < Mv; g++) {
+            const uint64_t n = p[g] * q[g];
+            if (p[g] < 2 || q[g] < 2 || a[g] < 1 || a[g] >= Q || m[g] >= n || s[g] == 0 ||
+                s[g] >= Q)
+                return OR_ERR_ARG;
+            s[g] = or_skip_next_direct(s[g], a[g], Q);
+            m[g] = or_addmod(m[g], s[g] % n, n);
+            const uint64_t c = or_encrypt_direct(m[g], e[g], n);
+            if (c_out)
+                c_out[k * Mv + g] = c;
+            if (r_out)
+                r_out[k * Mv + g] = or_unit(c, n);
+        }
+    }
+    return OR_OK;
 }
 
 int or_max_threads(void)

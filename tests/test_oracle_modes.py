@@ -184,3 +184,37 @@ def test_exact_and_paper_readings_differ_often():
     cs = [rng.randrange(n) for _ in range(20000)]
     diff = sum(oracle.unit(c, n) != oracle.unit_exact(c, n) for c in cs)
     assert diff > 0.1 * len(cs)
+
+
+def test_vector_call_is_the_interleaved_streams():
+    """Eq. vectorize: the Mv-vector update equals the Mv streams interleaved k-major, for
+    split substreams (Sec. VI) and for unrelated instances."""
+    p, q, e, m0 = _pq(700)
+    Mv, N = 8, 501
+    s0 = [oracle.split_s0(1, A, Mv, g) for g in range(Mv)]
+    pv = np.full(Mv, p, np.uint64)
+    qv = np.full(Mv, q, np.uint64)
+    ev = np.full(Mv, e, np.uint64)
+    av = np.full(Mv, A, np.uint64)
+    m = np.full(Mv, m0, np.uint64)
+    s = np.array(s0, np.uint64)
+    c, r = oracle.generate_vector(pv, qv, ev, av, m, s, N)
+    for g in range(Mv):
+        cg, rg, mg, sg = oracle.generate(p, q, e, m0, s0[g], N)
+        np.testing.assert_array_equal(c[g::Mv], cg)
+        np.testing.assert_array_equal(r[g::Mv].view(np.uint64), rg.view(np.uint64))
+        assert (int(m[g]), int(s[g])) == (mg, sg)
+    # substream 0 continues the parent; substream 1 is the parent shifted by (Q-1)/Mv skips
+    assert int(s0[1]) == pow(A, (Q - 1) // Mv, Q)
+    # unrelated instances, one with a constant skip
+    insts = [_pq(701), _pq(702), _pq(703)]
+    pv = np.array([x[0] for x in insts], np.uint64)
+    qv = np.array([x[1] for x in insts], np.uint64)
+    ev = np.array([x[2] for x in insts], np.uint64)
+    av = np.array([A, 1, A], np.uint64)
+    m = np.array([x[3] for x in insts], np.uint64)
+    s = np.array([1, 99, 1], np.uint64)
+    c, _ = oracle.generate_vector(pv, qv, ev, av, m, s, 300)
+    for g, (pp, qq, ee, mm) in enumerate(insts):
+        cg, _, _, _ = oracle.generate(pp, qq, ee, mm, [1, 99, 1][g], 300, a=int(av[g]))
+        np.testing.assert_array_equal(c[g::3], cg)

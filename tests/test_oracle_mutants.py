@@ -204,8 +204,30 @@ def check_unit_exact(L):
     return True
 
 
+def check_vector(L):
+    # Eq. vectorize: Mv = 3 instances side by side equal their streams interleaved k-major
+    ps = [2147483659, 2147483693, 4294967291]
+    qs = [2147483693, 4294967279, 2147483659]
+    es, N = [5, 7, 5], 40
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    arr = lambda xs: np.array(xs, np.uint64)
+    p, q, e, a = arr(ps), arr(qs), arr(es), arr([A, A, A])
+    m, s = arr([11, 22, 33]), arr([1, 1, 1])
+    c = np.zeros(3 * N, np.uint64)
+    if L.or_generate_vector(3, *(x.ctypes.data_as(u64p) for x in (p, q, e, a)), Q,
+                            m.ctypes.data_as(u64p), s.ctypes.data_as(u64p), N,
+                            c.ctypes.data_as(u64p), None) != 0:
+        return False
+    for g in range(3):
+        rc, cg, _, _, _ = _gen(L, ps[g], qs[g], es[g], [11, 22, 33][g], 1, N)
+        if rc != 0 or not (c[g::3] == cg).all():
+            return False
+    return True
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
-          check_rsa, check_unit, check_split, check_histogram, check_modes, check_unit_exact]
+          check_rsa, check_unit, check_split, check_histogram, check_modes, check_unit_exact,
+          check_vector]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -233,6 +255,7 @@ MUTANTS = {
     "unit_skip_rejected": ("a < 1 || a >= Q", "a < 2 || a >= Q"),
     "crt_exponent_wrong_modulus": ("return ra + a * t;", "return ra + b * t;"),
     "exact_division_truncates": ("    if (round_bit && (sticky || (m & 1)))\n        m++;\n", ""),
+    "vector_substream_major": ("                c_out[k * Mv + g] = c;", "                c_out[g * N + k] = c;"),
 }
 
 
