@@ -377,6 +377,47 @@ def form_fused(R, torch, device, peak_alu, rank) -> dict:
     return out
 
 
+def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 256) -> dict:
+    """The vectorised call of Sec. VI: a slice of the split workload (parents x 32 substreams
+    x 2^16, e = 3 or the next valid odd, u64 + f64), every parent's k-major vector in one
+    call; the substream-major batch over the same children is timed beside it."""
+    cfg = workload.CONFIGS["split_65536x32x2^16"]
+    mv, n = cfg["substreams"], cfg["count"]
+    ctx = R.Context(parents * (mv + 1), device=device)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], parents, first=rank * parents),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    kids = [ctx.split(first + i, mv) for i in range(parents)]
+    per = mv * n
+    oc = torch.empty(parents * per, dtype=torch.int64, device="cuda")
+    orr = torch.empty(parents * per, dtype=torch.float64, device="cuda")
+
+    groups = np.stack(kids).astype(np.uint32)
+
+    def vector_calls():
+        ctx.generate_interleaved(groups, n, out_r=orr, out_c=oc)
+
+    all_ids = groups.reshape(-1)
+    counts = np.full(len(all_ids), n, np.uint64)
+    out = {}
+    for name, fn in (("interleaved", vector_calls),
+                     ("substream_major", lambda: ctx.generate_batch(all_ids, counts, out_r=orr,
+                                                                    out_c=oc))):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        dt = a.elapsed_time(b) / 1e3
+        out[name] = {"value": round(parents * per / dt / 1e9, 3), "unit": UNIT,
+                     "ms": round(dt * 1e3, 2), "hbm_GBps": round(16 * parents * per / dt / 1e9, 1)}
+    out["shape"] = f"{parents} parents x {mv} substreams x {n}, u64 + f64, one call"
+    ctx.close()
+    del oc, orr
+    torch.cuda.empty_cache()
+    return out
+
+
 def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
     [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
@@ -562,6 +603,7 @@ def run_ours(args) -> int:
             "batched_1e5_lognormal": form_batched(R, torch, dist.local_rank, peak_alu, dist.rank),
             "serving_1e6": form_served(R, torch, dist.local_rank, peak_alu, dist.rank),
             "fused_histogram_bulk": form_fused(R, torch, dist.local_rank, peak_alu, dist.rank),
+            "split_interleaved": form_interleaved(R, torch, dist.local_rank, peak_alu, dist.rank),
         }
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)

@@ -238,6 +238,21 @@ int rsaprng_generate_batch_host(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_i
                                 const uint64_t *counts, const uint64_t *out_offsets, double *h_r,
                                 uint64_t *h_c, void *stream);
 
+/* The vectorised call of Sec. VI (Eq. vectorize), for ngroups vectors at once
+ * (one per process of the paper): group g is the Mv instances
+ * ids[g Mv .. g Mv + Mv) (typically the substreams of one rsaprng_split);
+ * they advance together by N outputs each, and the outputs are written
+ * k-major, the order in which the vector update returns them:
+ * d_r[g N Mv + k Mv + gamma] = r_{k+1} of instance ids[g Mv + gamma] (d_c
+ * likewise; either may be NULL), for k < N. Every instance advances by N.
+ * ids is a HOST array of ngroups Mv distinct ids; the outputs are DEVICE
+ * arrays of ngroups N Mv elements. Asynchronous on stream. Errors:
+ * RSAPRNG_ERR_ARG (Mv = 0, no output, repeated id), RSAPRNG_ERR_ID,
+ * RSAPRNG_ERR_CUDA. */
+int rsaprng_generate_interleaved(rsaprng_ctx *ctx, uint64_t ngroups, uint32_t Mv,
+                                 const rsaprng_id *ids, uint64_t N, double *d_r, uint64_t *d_c,
+                                 void *stream);
+
 /* ------------------------------------------------ fused consumer (Sec. VII) */
 
 /* Digit sources of rsaprng_histogram. */

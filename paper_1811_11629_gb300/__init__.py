@@ -250,6 +250,20 @@ class Context:
                                                  _u64p(offsets), hp(h_r), hp(h_c),
                                                  _stream_ptr(stream)), "generate_batch_host")
 
+    def generate_interleaved(self, ids, n, out_r=None, out_c=None, stream=None):
+        """The vectorised call (rsaprng_generate_interleaved). ids: one vector (Mv ids)
+        or a 2-D array of ngroups vectors; output k of ids[g][j] at element
+        g * n * Mv + k * Mv + j of out_r / out_c (CUDA tensors)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        groups, mv = (1, ids.shape[0]) if ids.ndim == 1 else ids.shape
+        ids = ids.reshape(-1)
+        for t in (out_r, out_c):
+            if t is not None and t.numel() < n * len(ids):
+                raise ValueError("output shorter than n * ids.size")
+        check(self.L.rsaprng_generate_interleaved(self.h, groups, mv, _u32p(ids), n, _dptr(out_r),
+                                                  _dptr(out_c), _stream_ptr(stream)),
+              "generate_interleaved")
+
     def histogram(self, ids, counts, D: int, d: int, source: int = 0, hist=None, stream=None):
         """Frequency (D = 1) / serial (D > 1) test histogram of the next counts[i] outputs
         of ids[i] (rsaprng_histogram). hist: CUDA int64 tensor of d**D counters, added to;

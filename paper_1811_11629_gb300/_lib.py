@@ -74,6 +74,7 @@ SIGNATURES = {
     "rsaprng_generate_batch": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_generate_batch_host": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_histogram": (i32, [vp, u64, pu32, pu64, u32, u32, i32, vp, vp]),
+    "rsaprng_generate_interleaved": (i32, [vp, u64, u32, pu32, u64, vp, vp, vp]),
     "rsaprng_instance_create_crt": (i32, [vp, u64, u64, u64, u64, u64, u64, u64, pu32]),
     "rsaprng_get_exponents": (i32, [vp, u32, pu64, pu64]),
     "rsaprng_chi2_uniform": (i32, [pu64, u64, pdbl, pu64]),

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(BUILD, "librsaprng.so")
-SOURCES = ["kernels.cu", "consume.cu", "api.cu", "plans.cu", "server.cpp", "host_params.cpp",
-           "noalloc.cu"]
+SOURCES = ["kernels.cu", "consume.cu", "vector.cu", "api.cu", "plans.cu", "server.cpp",
+           "host_params.cpp", "noalloc.cu"]
 HEADERS = ["device_math.cuh", "kernels.cuh", "tile.cuh", "host_params.hpp", "api_internal.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -97,6 +97,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
                      bool want_c, int *occupancy)
 {
     GenLaunch g;
+    g.stride = 1;
     g.threads = cfg.threads_per_block;
     g.L = cfg.numbers_per_thread;
     g.modexp = cfg.modexp == RSAPRNG_MODEXP_MONT64 ? MODEXP_MONT64 : MODEXP_CRT32;
@@ -155,12 +156,15 @@ constexpr uint64_t kPiecesPerBlock = 1;
 
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
-               uint64_t tuple)
+               uint64_t tuple, uint64_t stride)
 {
     hp.items.clear();
     hp.chunks.clear();
     hp.groups.clear();
     hp.numbers = 0;
+    hp.stride = stride;
+    hp.vecs.clear();
+    hp.vec_ts = 0;
     if (chunk == 0)
         chunk = ~0ULL;
     // Group requests by instance, keeping array order inside each instance.
@@ -181,8 +185,18 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
     // Cost of one piece: the work spread over the resident blocks of the
     // launch, kPiecesPerBlock pieces each; pieces are whole tiles.
     const GenLaunch full = ctx_launch(c, cfg, ~0ULL, true, false);
-    const uint64_t tile = (uint64_t)full.threads * full.L * std::max<uint64_t>(1, tuple);
-    const uint64_t piece_cost = std::max<uint64_t>(1, work / ((uint64_t)full.grid * kPiecesPerBlock));
+    uint64_t tile = (uint64_t)full.threads * full.L * std::max<uint64_t>(1, tuple);
+    // The vector kernel puts G instances in a block, each with TS L positions
+    // per tile: pieces are whole tiles of it, and there are G times as many
+    // pieces to spread over the resident blocks.
+    uint64_t per_block = 1;
+    if (stride > 1) {
+        hp.vec_ts = vec_threads_per_instance(full.threads, stride);
+        per_block = (uint64_t)(full.threads / hp.vec_ts);
+        tile = (uint64_t)hp.vec_ts * full.L;
+    }
+    const uint64_t piece_cost =
+        std::max<uint64_t>(1, work / ((uint64_t)full.grid * kPiecesPerBlock * per_block));
     if (tuple > 1 && chunk != ~0ULL)
         chunk = std::max(tile, chunk / tile * tile);
     std::stable_sort(order.begin(), order.end(),
@@ -191,7 +205,7 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
         uint64_t offset, len, out;
     };
     std::vector<Piece> pieces;
-    std::vector<uint64_t> item_cost;
+    std::vector<uint64_t> item_cost, item_pos;
     for (uint64_t g0 = 0; g0 < nreq;) {
         uint64_t g1 = g0;
         const rsaprng_id id = ids[order[g0]];
@@ -215,7 +229,7 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
                 const uint64_t len = std::min(left, room);
                 pieces.push_back({off, len, out});
                 off += len;
-                out += len;
+                out += len * stride;
                 left -= len;
             }
         }
@@ -227,6 +241,7 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
             WorkItem it{id, WI_FROM_STATE | WI_WRITEBACK, pieces[0].len, pieces[0].out, 0, 0};
             hp.items.push_back(it);
             item_cost.push_back(pieces[0].len * w);
+            item_pos.push_back(0);
             continue;
         }
         PrepGroup grp{id, (uint32_t)hp.chunks.size(), (uint32_t)pieces.size(), 0};
@@ -239,16 +254,24 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
             hp.chunks.push_back(pc);
             hp.items.push_back(it);
             item_cost.push_back(pieces[k].len * w);
+            item_pos.push_back(pieces[k].offset);
         }
     }
     if (hp.items.size() > 0xFFFFFFF0ULL || hp.chunks.size() > 0xFFFFFFF0ULL)
         return fail(RSAPRNG_ERR_ARG, "plan too large");
-    // Longest-processing-time-first order for the persistent launch.
+    // Longest-processing-time-first order for the persistent launch. In the
+    // interleaved order (stride > 1) the outputs of different instances at
+    // the same position share memory sectors: pieces are ordered by position
+    // instead, so those writes happen side by side and merge in L2.
     std::vector<uint32_t> perm(hp.items.size()), where(hp.items.size());
     for (size_t i = 0; i < perm.size(); i++)
         perm[i] = (uint32_t)i;
-    std::stable_sort(perm.begin(), perm.end(),
-                     [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
+    if (stride > 1)
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](uint32_t x, uint32_t y) { return item_pos[x] < item_pos[y]; });
+    else
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
     std::vector<WorkItem> sorted(hp.items.size());
     for (size_t i = 0; i < perm.size(); i++) {
         sorted[i] = hp.items[perm[i]];
@@ -257,6 +280,20 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
     hp.items.swap(sorted);
     for (auto &pc : hp.chunks)
         pc.item = where[pc.item];
+    if (stride > 1) {
+        // Units of the vector kernel: up to G items in a row with the same
+        // length whose outputs are neighbours (consecutive instances of a
+        // vector at the same positions).
+        const uint32_t G = (uint32_t)(full.threads / hp.vec_ts);
+        for (uint32_t i = 0; i < (uint32_t)hp.items.size();) {
+            uint32_t j = i + 1;
+            while (j < hp.items.size() && j - i < G && hp.items[j].count == hp.items[i].count &&
+                   hp.items[j].out_off == hp.items[j - 1].out_off + 1)
+                j++;
+            hp.vecs.push_back({i, j - i});
+            i = j;
+        }
+    }
     return RSAPRNG_OK;
 }
 
@@ -300,8 +337,9 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     const size_t b_items = hp.items.size() * sizeof(WorkItem);
     const size_t b_chunks = hp.chunks.size() * sizeof(PrepChunk);
     const size_t b_groups = hp.groups.size() * sizeof(PrepGroup);
+    const size_t b_vecs = hp.vecs.size() * sizeof(VecGroup);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t total = al(b_items) + al(b_chunks) + al(b_groups) + 256;
+    const size_t total = al(b_items) + al(b_chunks) + al(b_groups) + al(b_vecs) + 256;
     int rc;
     if ((rc = grow(&dp.d_buf, &dp.cap_buf, total)) != RSAPRNG_OK)
         return rc;
@@ -322,6 +360,9 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     dp.groups = (PrepGroup *)(d + o);
     memcpy(h + o, hp.groups.data(), b_groups);
     o += al(b_groups);
+    dp.vecs = (VecGroup *)(d + o);
+    memcpy(h + o, hp.vecs.data(), b_vecs);
+    o += al(b_vecs);
     dp.ticket = (uint32_t *)(d + o);
     memset(h + o, 0, 256);
     o += 256;
@@ -331,11 +372,30 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     dp.nchunks = (uint32_t)hp.chunks.size();
     dp.ngroups = (uint32_t)hp.groups.size();
     dp.numbers = hp.numbers;
+    dp.stride = hp.stride;
+    dp.nvecs = (uint32_t)hp.vecs.size();
+    dp.vec_ts = hp.vec_ts;
     cudaError_t e = cudaMemcpyAsync(dp.d_buf, dp.h_buf, o, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "plan upload");
     c->h2d_bytes += o;
     return RSAPRNG_OK;
+}
+
+// Launch shape of the vector kernel (interleaved order) for cfg.
+static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nvecs, bool want_r,
+                            bool want_c)
+{
+    GenLaunch g = ctx_launch(c, cfg, nvecs, want_r, want_c);
+    int occ = vec_blocks_per_sm(g, vec_smem_bytes(g.threads, g.L, want_r, want_c));
+    if (occ < 1)
+        occ = 1;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ)
+        occ = cfg.blocks_per_sm;
+    const uint64_t resident = (uint64_t)occ * c->sms;
+    g.persistent = nvecs > resident;
+    g.grid = (int)(g.persistent ? resident : std::max<uint64_t>(nvecs, 1));
+    return g;
 }
 
 // Launch shape of the histogram consumer for cfg (its own occupancy).
@@ -369,9 +429,12 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         nl += 2;
     }
     if (dp.nitems) {
-        GenLaunch g = hist ? hist_launch(c, cfg, dp.nitems)
-                           : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr,
-                                        &dp.occupancy);
+        const bool vec = !hist && dp.stride > 1 && dp.nvecs;
+        GenLaunch g = hist  ? hist_launch(c, cfg, dp.nitems)
+                      : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr)
+                            : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr,
+                                         &dp.occupancy);
+        g.stride = dp.stride;
         dp.last = g;
         if (g.persistent) {
             if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
@@ -379,6 +442,9 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         }
         if (hist)
             e = launch_histogram(g, t, dp.items, dp.nitems, dp.ticket, *hist, stream);
+        else if (vec)
+            e = launch_generate_vec(g, t, dp.items, dp.vecs, dp.nvecs, dp.ticket, d_r, d_c,
+                                    dp.vec_ts, stream);
         else
             e = launch_generate(g, t, dp.items, dp.nitems, dp.ticket, d_r, d_c, stream);
         if (e != cudaSuccess)
@@ -839,6 +905,44 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
         return rc;
     if (hp.items.empty())
         return RSAPRNG_OK;
+    ScratchSlot *slot;
+    if ((rc = scratch_slot(c, &slot)) != RSAPRNG_OK)
+        return rc;
+    if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
+        return rc;
+    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr);
+    cudaEventRecord(slot->done, st);
+    slot->used = true;
+    return rc;
+}
+
+int rsaprng_generate_interleaved(rsaprng_ctx *c, uint64_t ngroups, uint32_t Mv,
+                                 const rsaprng_id *ids, uint64_t N, double *d_r, uint64_t *d_c,
+                                 void *stream)
+{
+    if (!c || Mv == 0 || (ngroups && !ids))
+        return fail(RSAPRNG_ERR_ARG, "generate_interleaved: bad arguments");
+    if (!d_r && !d_c)
+        return fail(RSAPRNG_ERR_ARG, "generate_interleaved: no output buffer");
+    const uint64_t k = ngroups * Mv;
+    std::vector<rsaprng_id> sorted(ids, ids + k);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return fail(RSAPRNG_ERR_ARG, "generate_interleaved: an instance appears twice");
+    if (N == 0 || k == 0)
+        return RSAPRNG_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Instance gamma of group g: output k goes to element g N Mv + k Mv + gamma.
+    const std::vector<uint64_t> counts(k, N);
+    std::vector<uint64_t> offs(k);
+    for (uint64_t g = 0; g < ngroups; g++)
+        for (uint32_t j = 0; j < Mv; j++)
+            offs[g * Mv + j] = g * N * Mv + j;
+    HostPlan hp;
+    int rc = build_plan(c, c->cfg, k, ids, counts.data(), offs.data(), c->cfg.chunk, hp, 1, Mv);
+    if (rc)
+        return rc;
     ScratchSlot *slot;
     if ((rc = scratch_slot(c, &slot)) != RSAPRNG_OK)
         return rc;

@@ -18,6 +18,9 @@ struct HostPlan {
     std::vector<PrepChunk> chunks;
     std::vector<PrepGroup> groups;
     uint64_t numbers = 0;
+    uint64_t stride = 1;  // element distance between consecutive outputs of a request
+    std::vector<VecGroup> vecs;  // stride > 1: blocks' units of the vector kernel
+    int vec_ts = 0;              // threads per instance in the vector kernel
 };
 
 // The same lists in device memory (one allocation) plus the skip-sum scratch.
@@ -36,6 +39,10 @@ struct DevPlan {
     uint64_t *chunk_s = nullptr;
     uint32_t nitems = 0, nchunks = 0, ngroups = 0;
     uint64_t numbers = 0;
+    uint64_t stride = 1;
+    VecGroup *vecs = nullptr;
+    uint32_t nvecs = 0;
+    int vec_ts = 0;
     GenLaunch last{};  // shape of the most recent generation launch
     int occupancy = 0; // resident blocks per SM of that launch
 };
@@ -76,10 +83,11 @@ DeviceTables ctx_tables(rsaprng_ctx *c);
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,
                      bool want_c, int *occupancy = nullptr);
 // Pieces of a stream are whole tiles; with tuple > 1 they are also whole
-// multiples of tuple outputs (the histogram consumer's D-tuples).
+// multiples of tuple outputs (the histogram consumer's D-tuples). Output k of
+// request i goes to element offsets[i] + k stride.
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
-               uint64_t tuple = 1);
+               uint64_t tuple = 1, uint64_t stride = 1);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
 // Launches the pre-pass and the generation kernel, or the histogram
 // consumer instead of the generation kernel when hist is given.

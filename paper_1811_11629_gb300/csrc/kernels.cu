@@ -40,7 +40,7 @@ template <int L, int MODEXP, int DIV>
 __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
                                                   uint32_t nitems, uint32_t *ticket,
                                                   double *__restrict__ out_r,
-                                                  u64 *__restrict__ out_c)
+                                                  u64 *__restrict__ out_c, u64 stride)
 {
     extern __shared__ u64 smem[];
     __shared__ u64 sh_scan[32];
@@ -92,14 +92,27 @@ __global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkIt
                     st_c[i] = c[j];
             }
             __syncthreads();
-            const u64 o = W.out_off + base;
-            if (out_r) {
-                for (int i = t; i < tile_n; i += T)
-                    out_r[o + i] = __longlong_as_double((long long)st_r[sidx(i)]);
-            }
-            if (out_c) {
-                for (int i = t; i < tile_n; i += T)
-                    out_c[o + i] = st_c[sidx(i)];
+            if (stride == 1) {
+                const u64 o = W.out_off + base;
+                if (out_r) {
+                    for (int i = t; i < tile_n; i += T)
+                        out_r[o + i] = __longlong_as_double((long long)st_r[sidx(i)]);
+                }
+                if (out_c) {
+                    for (int i = t; i < tile_n; i += T)
+                        out_c[o + i] = st_c[sidx(i)];
+                }
+            } else {  // interleaved order: outputs of the item stride elements apart
+                const u64 o = W.out_off + base * stride;
+                if (out_r) {
+                    for (int i = t; i < tile_n; i += T)
+                        out_r[o + (u64)i * stride] =
+                            __longlong_as_double((long long)st_r[sidx(i)]);
+                }
+                if (out_c) {
+                    for (int i = t; i < tile_n; i += T)
+                        out_c[o + (u64)i * stride] = st_c[sidx(i)];
+                }
             }
             __syncthreads();
             m = addmod(m, total, n);
@@ -232,7 +245,7 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
             return e;
     }
     kern<<<g.grid, g.threads, smem, stream>>>(t, items, nitems, g.persistent ? ticket : nullptr,
-                                              out_r, out_c);
+                                              out_r, out_c, g.stride);
     return cudaGetLastError();
 }
 

@@ -17,8 +17,9 @@ constexpr int kMaxTile = kMaxThreads * kMaxL;
 constexpr int kPowLinRow = kMaxTile + 1;
 
 // One unit of work for the generation kernel: `count` consecutive outputs of
-// instance `inst` written at element `out_off` of the output arrays, starting
-// from the state (m0, s0) before the first output.
+// instance `inst` written from element `out_off` of the output arrays (one
+// element apart, or a launch-wide stride apart for the interleaved order),
+// starting from the state (m0, s0) before the first output.
 enum : uint32_t {
     WI_FROM_STATE = 1u,  // take (m0, s0) from the instance state table
     WI_WRITEBACK = 2u,   // store the state after the last output
@@ -72,10 +73,28 @@ struct GenLaunch {
     int divide;      // Divide
     int grid;        // blocks
     bool persistent; // items pulled from *ticket
+    uint64_t stride; // element distance between consecutive outputs of a work item
 };
 
 // Shared memory bytes the generation kernel needs for a tile.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
+
+// The interleaved (vector) order: a block takes up to G = threads / TS work
+// items that cover the same positions of consecutive instances of a vector
+// (items first .. first+count-1, output elements one apart).
+struct VecGroup {
+    uint32_t first;
+    uint32_t count;
+};
+size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c);
+// Threads per instance (TS) for a block of `threads` and a vector of `stride`
+// instances: G = threads / TS instances per block, the smallest power of two
+// >= stride between threads / 32 and threads / 4.
+int vec_threads_per_instance(int threads, uint64_t stride);
+cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                                const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
+                                double *out_r, uint64_t *out_c, int TS, cudaStream_t stream);
+int vec_blocks_per_sm(const GenLaunch &g, size_t smem);
 
 // Histogram consumer: d^D counters at hist; digits of r (low = 0) or of the
 // low bits of c (low = 1, d a power of two); D in [1, 8].

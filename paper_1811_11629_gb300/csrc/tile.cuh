@@ -89,19 +89,37 @@ __device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
         return (j & 3) == 3 ? dev::unit_int_fast(c, P) : dev::unit_recip(c, P.dn, P.recip);
 }
 
+// Exclusive scan of v (mod n) over segments of TS consecutive lanes (TS a
+// power of two <= 32, segments aligned in the warp); total receives the
+// segment's sum. No barrier: a segment lives in one warp.
+__device__ __forceinline__ u64 segment_exscan_mod(u64 v, u64 n, int TS, u64 &total)
+{
+    const int lt = threadIdx.x & (TS - 1);
+    u64 incl = v;
+    for (int d = 1; d < TS; d <<= 1) {
+        const u64 o = __shfl_up_sync(FULL, incl, d, TS);
+        if (lt >= d)
+            incl = addmod(incl, o, n);
+    }
+    total = __shfl_sync(FULL, incl, TS - 1, TS);
+    const u64 ex = __shfl_up_sync(FULL, incl, 1, TS);
+    return lt == 0 ? 0 : ex;
+}
+
 // Steps 1-3 of a tile for the calling thread, which owns outputs my0+1 ..
-// my0+L of the tile: its skips from s_thr (the skip before its run), the
-// block scan of their sums mod n, its messages from the carry m (the message
-// before the tile), and their L ciphertexts. Entries at or past nvalid are
-// computed but meaningless. The thread that owns the stream's last output
-// (left = outputs from the tile start to the end of the work item) writes the
-// instance's skip back when the item asks for it. total returns the tile's
-// skip sum mod n (the carry to the next tile). Contains two __syncthreads().
-template <int L, int MODEXP>
-__device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const WorkItem &W,
-                                                 const InstParams &P, u64 m, u64 s_thr, u64 left,
-                                                 int my0, int nvalid, u64 *sh_scan, u64 (&c)[L],
-                                                 u64 &total)
+// my0+L of its stream's tile: its skips from s_thr (the skip before its run),
+// the scan of their sums mod n over the threads of the stream (scan(sum, n,
+// total) returns the exclusive prefix), its messages from the carry m (the
+// message before the tile), and their L ciphertexts. Entries at or past
+// nvalid are computed but meaningless. The thread that owns the stream's last
+// output (left = outputs from the tile start to the end of the work item)
+// writes the instance's skip back when the item asks for it. total returns
+// the tile's skip sum mod n (the carry to the next tile).
+template <int L, int MODEXP, class Scan>
+__device__ __forceinline__ void tile_ciphertexts_scan(const DeviceTables &tab, const WorkItem &W,
+                                                      const InstParams &P, u64 m, u64 s_thr,
+                                                      u64 left, int my0, int nvalid, Scan &&scan,
+                                                      u64 (&c)[L], u64 &total)
 {
     const u64 n = P.n, r64 = P.r64;
     const u32 a = P.a;
@@ -117,7 +135,7 @@ __device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const 
         }
     }
     sum = reduce_u64(sum, n);
-    const u64 pre = block_exscan_mod(sum, n, sh_scan, total);
+    const u64 pre = scan(sum, n, total);
     u64 msg[L];
     u64 mm = addmod(m, pre, n);
 #pragma unroll
@@ -128,6 +146,19 @@ __device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const 
     if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
         tab.state_s[W.inst] = s_last;  // this thread owns the stream's last output
     encrypt<L, MODEXP>(msg, c, P);
+}
+
+// The same for one stream per block: the block-wide scan (two
+// __syncthreads()).
+template <int L, int MODEXP>
+__device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const WorkItem &W,
+                                                 const InstParams &P, u64 m, u64 s_thr, u64 left,
+                                                 int my0, int nvalid, u64 *sh_scan, u64 (&c)[L],
+                                                 u64 &total)
+{
+    tile_ciphertexts_scan<L, MODEXP>(
+        tab, W, P, m, s_thr, left, my0, nvalid,
+        [&](u64 v, u64 n, u64 &tot) { return block_exscan_mod(v, n, sh_scan, tot); }, c, total);
 }
 
 }  // namespace tile

@@ -1,0 +1,250 @@
+// The vectorised call of Sec. VI (Eq. vectorize) on the tile engine: the
+// outputs of Mv instances come back k-major (element k Mv + gamma), so the
+// outputs of one instance lie Mv elements apart. Written one instance per
+// block, every store would fill one element of a memory sector that other
+// blocks complete later, and the memory would read and rewrite each sector.
+// Here a block takes G instances of one vector side by side at the same
+// positions: TS = T / G threads per instance, each owning L consecutive
+// outputs of its instance, so a tile holds K = TS L positions of G
+// instances. The skip scan of an instance runs over its TS lanes
+// (segmented shuffles, no barrier); the tile is staged k-major in shared
+// memory and written as rows of G consecutive elements.
+//
+// The plan is the ordinary one (pieces, skip-sum pre-pass, start states);
+// the host groups up to G work items that cover the same positions of
+// consecutive instances of a vector into one block's unit (VecGroup).
+#include "device_math.cuh"
+#include "kernels.cuh"
+#include "tile.cuh"
+
+namespace rsaprng {
+
+namespace {
+
+using dev::addmod;
+using dev::mulmodQ;
+using tile::to_unit;
+
+template <int L, int MODEXP, int DIV>
+__global__ void __launch_bounds__(512)
+    k_generate_vec(DeviceTables tab, const WorkItem *__restrict__ items,
+                   const VecGroup *__restrict__ vecs, uint32_t nvecs, uint32_t *ticket,
+                   double *__restrict__ out_r, u64 *__restrict__ out_c, u64 stride, int TS)
+{
+    extern __shared__ u64 smem[];
+    __shared__ uint32_t sh_item;
+    const int T = blockDim.x, t = threadIdx.x;
+    const int tsh = __ffs(TS) - 1, G = T >> tsh, gsh = __ffs(G) - 1;  // both powers of two
+    const int seg = t >> tsh, lt = t & (TS - 1);
+    const int K = TS * L;  // positions of each instance per tile
+    const int S = K * G;   // = T L outputs per tile
+    const int my0 = lt * L;
+    u64 *st_r = smem;
+    u64 *st_c = smem + (out_r ? S : 0);
+
+    uint32_t v = blockIdx.x;
+    if (ticket) {
+        if (t == 0)
+            sh_item = atomicAdd(ticket, 1u);
+        __syncthreads();
+        v = sh_item;
+    }
+    while (v < nvecs) {
+        const VecGroup V = vecs[v];
+        const bool on = seg < (int)V.count;
+        // Idle segments shadow the first item: they compute alongside (the
+        // shuffles need every lane) but store and write back nothing.
+        const WorkItem W = items[V.first + (on ? seg : 0)];
+        const InstParams P = tab.params[W.inst];
+        const u64 n = P.n;
+        const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
+        u64 m, s;
+        if (W.flags & WI_FROM_STATE) {
+            m = tab.state_m[W.inst];
+            s = tab.state_s[W.inst];
+        } else {
+            m = W.m0;
+            s = W.s0;
+        }
+        u64 s_thr = mulmodQ(s, plin[my0]);
+        const u64 aK = plin[K];
+        const u64 count = W.count;  // the same for every item of the group
+        const u64 o0 = items[V.first].out_off;
+        WorkItem Wb = W;
+        if (!on)
+            Wb.flags &= ~(uint32_t)WI_WRITEBACK;
+        for (u64 base = 0; base < count; base += K) {
+            const u64 left = count - base;
+            const int tile_n = left < (u64)K ? (int)left : K;
+            const int nvalid = !on ? 0 : (tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0));
+            u64 c[L], total;
+            tile::tile_ciphertexts_scan<L, MODEXP>(
+                tab, Wb, P, m, s_thr, left, my0, nvalid,
+                [&](u64 x, u64 nn, u64 &tot) { return tile::segment_exscan_mod(x, nn, TS, tot); },
+                c, total);
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                const int i = (my0 + j) * G + seg;  // row = position, column = instance
+                if (out_r)
+                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
+                if (out_c)
+                    st_c[i] = c[j];
+            }
+            __syncthreads();
+            const int cols = (int)V.count;
+            for (int i = t; i < tile_n * G; i += T) {
+                const int col = i & (G - 1);
+                if (col < cols) {
+                    const u64 e = o0 + (base + (u64)(i >> gsh)) * stride + (u64)col;
+                    if (out_r)
+                        out_r[e] = __longlong_as_double((long long)st_r[i]);
+                    if (out_c)
+                        out_c[e] = st_c[i];
+                }
+            }
+            __syncthreads();
+            m = addmod(m, total, n);
+            s_thr = mulmodQ(s_thr, aK);
+        }
+        if (on && lt == 0 && (W.flags & WI_WRITEBACK)) {
+            tab.state_m[W.inst] = m;
+            if (count == 0)
+                tab.state_s[W.inst] = s;
+        }
+        if (ticket) {
+            __syncthreads();
+            if (t == 0)
+                sh_item = atomicAdd(ticket, 1u);
+            __syncthreads();
+            v = sh_item;
+        } else {
+            v += gridDim.x;
+        }
+    }
+}
+
+// Every division route gives the same bits, so the vector kernel is
+// instantiated for the integer and reciprocal routes (the others map to the
+// reciprocal one) and for the exact-rational reading.
+template <int DIV>
+const void *vec_kernel_ptr_d(int L, int modexp)
+{
+    if (modexp == MODEXP_CRT32) {
+        if (L == 16)
+            return (const void *)k_generate_vec<16, MODEXP_CRT32, DIV>;
+        if (L == 8)
+            return (const void *)k_generate_vec<8, MODEXP_CRT32, DIV>;
+        if (L == 4)
+            return (const void *)k_generate_vec<4, MODEXP_CRT32, DIV>;
+        if (L == 2)
+            return (const void *)k_generate_vec<2, MODEXP_CRT32, DIV>;
+    } else {
+        if (L == 8)
+            return (const void *)k_generate_vec<8, MODEXP_MONT64, DIV>;
+        if (L == 4)
+            return (const void *)k_generate_vec<4, MODEXP_MONT64, DIV>;
+        if (L == 2)
+            return (const void *)k_generate_vec<2, MODEXP_MONT64, DIV>;
+    }
+    return nullptr;
+}
+
+int vec_div(int divide)
+{
+    return divide == DIVIDE_EXACT ? DIVIDE_EXACT : divide == DIVIDE_INT ? DIVIDE_INT : DIVIDE_RECIP;
+}
+
+const void *vec_kernel_ptr(const GenLaunch &g)
+{
+    switch (vec_div(g.divide)) {
+    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp);
+    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp);
+    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp);
+    }
+}
+
+template <int L, int MODEXP, int DIV>
+cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                         const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
+                         uint64_t *out_c, int TS, cudaStream_t stream)
+{
+    const size_t smem = vec_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
+    auto kern = k_generate_vec<L, MODEXP, DIV>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    kern<<<g.grid, g.threads, smem, stream>>>(t, items, vecs, nvecs,
+                                              g.persistent ? ticket : nullptr, out_r, out_c,
+                                              g.stride, TS);
+    return cudaGetLastError();
+}
+
+template <int DIV>
+cudaError_t launch_vec_d(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                         const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
+                         uint64_t *out_c, int TS, cudaStream_t stream)
+{
+#define RSAPRNG_VEC(LL, MM)                                                                   \
+    if (g.L == LL && g.modexp == MM)                                                          \
+        return launch_vec_t<LL, MM, DIV>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS, \
+                                         stream);
+    RSAPRNG_VEC(16, MODEXP_CRT32)
+    RSAPRNG_VEC(8, MODEXP_CRT32)
+    RSAPRNG_VEC(4, MODEXP_CRT32)
+    RSAPRNG_VEC(2, MODEXP_CRT32)
+    RSAPRNG_VEC(8, MODEXP_MONT64)
+    RSAPRNG_VEC(4, MODEXP_MONT64)
+    RSAPRNG_VEC(2, MODEXP_MONT64)
+#undef RSAPRNG_VEC
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
+{
+    return (size_t)threads * L * 8 * ((want_r ? 1 : 0) + (want_c ? 1 : 0));
+}
+
+int vec_threads_per_instance(int threads, uint64_t stride)
+{
+    int G = threads / 4;  // at most: four threads per instance
+    while (G > threads / 32 && (uint64_t)(G / 2) >= stride)
+        G /= 2;
+    return threads / G;
+}
+
+cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                                const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
+                                double *out_r, uint64_t *out_c, int TS, cudaStream_t stream)
+{
+    switch (vec_div(g.divide)) {
+    case DIVIDE_EXACT:
+        return launch_vec_d<DIVIDE_EXACT>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+                                          stream);
+    case DIVIDE_INT:
+        return launch_vec_d<DIVIDE_INT>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+                                        stream);
+    default:
+        return launch_vec_d<DIVIDE_RECIP>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+                                          stream);
+    }
+}
+
+int vec_blocks_per_sm(const GenLaunch &g, size_t smem)
+{
+    const void *k = vec_kernel_ptr(g);
+    if (!k)
+        return 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, g.threads, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+}  // namespace rsaprng
