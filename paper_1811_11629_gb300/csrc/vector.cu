@@ -7,8 +7,8 @@
 // positions: TS = T / G threads per instance, each owning L consecutive
 // outputs of its instance, so a tile holds K = TS L positions of G
 // instances. The skip scan of an instance runs over its TS lanes
-// (segmented shuffles, no barrier); the tile is staged k-major in shared
-// memory and written as rows of G consecutive elements.
+// (segmented shuffles, no barrier); the tile is staged instance by instance
+// in shared memory and written k-major, as rows of G consecutive elements.
 //
 // The plan is the ordinary one (pieces, skip-sum pre-pass, start states);
 // the host groups up to G work items that cover the same positions of
@@ -23,6 +23,7 @@ namespace {
 
 using dev::addmod;
 using dev::mulmodQ;
+using tile::sidx;
 using tile::to_unit;
 
 template <int L, int MODEXP, int DIV>
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(512)
     const int S = K * G;   // = T L outputs per tile
     const int my0 = lt * L;
     u64 *st_r = smem;
-    u64 *st_c = smem + (out_r ? S : 0);
+    u64 *st_c = smem + (out_r ? S + (S >> 4) : 0);
 
     uint32_t v = blockIdx.x;
     if (ticket) {
@@ -54,7 +55,9 @@ __global__ void __launch_bounds__(512)
         const bool on = seg < (int)V.count;
         // Idle segments shadow the first item: they compute alongside (the
         // shuffles need every lane) but store and write back nothing.
-        const WorkItem W = items[V.first + (on ? seg : 0)];
+        WorkItem W = items[V.first + (on ? seg : 0)];
+        if (!on)
+            W.flags &= ~(uint32_t)WI_WRITEBACK;
         const InstParams P = tab.params[W.inst];
         const u64 n = P.n;
         const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
@@ -70,43 +73,42 @@ __global__ void __launch_bounds__(512)
         const u64 aK = plin[K];
         const u64 count = W.count;  // the same for every item of the group
         const u64 o0 = items[V.first].out_off;
-        WorkItem Wb = W;
-        if (!on)
-            Wb.flags &= ~(uint32_t)WI_WRITEBACK;
         for (u64 base = 0; base < count; base += K) {
             const u64 left = count - base;
             const int tile_n = left < (u64)K ? (int)left : K;
             const int nvalid = !on ? 0 : (tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0));
             u64 c[L], total;
             tile::tile_ciphertexts_scan<L, MODEXP>(
-                tab, Wb, P, m, s_thr, left, my0, nvalid,
+                tab, W, P, m, s_thr, left, my0, nvalid,
                 [&](u64 x, u64 nn, u64 &tot) { return tile::segment_exscan_mod(x, nn, TS, tot); },
                 c, total);
+            // staged by instance: slot seg K + position (padded every 16)
+            const int row0 = seg * K + my0;
 #pragma unroll
             for (int j = 0; j < L; j++) {
-                const int i = (my0 + j) * G + seg;  // row = position, column = instance
                 if (out_r)
-                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
+                    st_r[sidx(row0 + j)] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
                 if (out_c)
-                    st_c[i] = c[j];
+                    st_c[sidx(row0 + j)] = c[j];
             }
             __syncthreads();
             const int cols = (int)V.count;
             for (int i = t; i < tile_n * G; i += T) {
-                const int col = i & (G - 1);
+                const int col = i & (G - 1), k = i >> gsh;  // written k-major
                 if (col < cols) {
-                    const u64 e = o0 + (base + (u64)(i >> gsh)) * stride + (u64)col;
+                    const u64 e = o0 + (base + (u64)k) * stride + (u64)col;
+                    const int slot = sidx(col * K + k);
                     if (out_r)
-                        out_r[e] = __longlong_as_double((long long)st_r[i]);
+                        out_r[e] = __longlong_as_double((long long)st_r[slot]);
                     if (out_c)
-                        out_c[e] = st_c[i];
+                        out_c[e] = st_c[slot];
                 }
             }
             __syncthreads();
             m = addmod(m, total, n);
             s_thr = mulmodQ(s_thr, aK);
         }
-        if (on && lt == 0 && (W.flags & WI_WRITEBACK)) {
+        if (lt == 0 && (W.flags & WI_WRITEBACK)) {
             tab.state_m[W.inst] = m;
             if (count == 0)
                 tab.state_s[W.inst] = s;
@@ -206,7 +208,7 @@ cudaError_t launch_vec_d(const GenLaunch &g, const DeviceTables &t, const WorkIt
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
 {
-    return (size_t)threads * L * 8 * ((want_r ? 1 : 0) + (want_c ? 1 : 0));
+    return gen_smem_bytes(threads, L, want_r, want_c);  // the same padded slots
 }
 
 int vec_threads_per_instance(int threads, uint64_t stride)
