@@ -201,7 +201,8 @@ def imad_slots_per_number(e: int) -> int:
 
 KERNEL_SOURCES = ["paper_1811_11629_gb300/csrc/kernels.cu",
                   "paper_1811_11629_gb300/csrc/device_math.cuh",
-                  "paper_1811_11629_gb300/csrc/kernels.cuh"]
+                  "paper_1811_11629_gb300/csrc/kernels.cuh",
+                  "paper_1811_11629_gb300/csrc/tile.cuh"]
 TRAFFIC_PROFILE = "profiles/dram_traffic_bulk_1024x2p20.md"
 
 
