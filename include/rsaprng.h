@@ -230,10 +230,11 @@ int rsaprng_generate_batch(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *id
                            const uint64_t *counts, const uint64_t *out_offsets, double *d_r,
                            uint64_t *d_c, void *stream);
 
-/* The same with HOST output buffers (end to end): the library copies the
- * outputs device->host itself, overlapping copies with generation, and
- * returns when h_r / h_c hold the results. Either may be NULL. Pinned host
- * memory is fastest. */
+/* The same with HOST output buffers (end to end); returns when h_r / h_c
+ * hold the results. Either may be NULL. Page-locked (pinned) buffers are
+ * written by the generation kernel itself over the CPU-GPU link; pageable
+ * buffers are filled by device slices copied device->host, overlapped with
+ * generation. */
 int rsaprng_generate_batch_host(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
                                 const uint64_t *counts, const uint64_t *out_offsets, double *h_r,
                                 uint64_t *h_c, void *stream);

@@ -182,6 +182,31 @@ int rsaprng_generate_batch_host(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id 
         total += counts[i];
     if (total == 0)
         return RSAPRNG_OK;
+    // Page-locked host buffers are mapped into the device's address space: the
+    // kernel stores straight into them over the CPU-GPU link (one launch, no
+    // staging). Pageable buffers go through device slices and copies below.
+    auto mapped = [](void *h) -> void * {
+        if (!h)
+            return nullptr;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    void *m_r = mapped(h_r), *m_c = mapped(h_c);
+    if ((!h_r || m_r) && (!h_c || m_c)) {
+        int rc = rsaprng_generate_batch(c, nreq, ids, counts, out_offsets, (double *)m_r,
+                                        (uint64_t *)m_c, stream);
+        if (rc)
+            return rc;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "host-output generation");
+        c->d2h_bytes += total * ((h_r ? 8 : 0) + (h_c ? 8 : 0));
+        return RSAPRNG_OK;
+    }
     const int nslices = (int)std::min<uint64_t>(8, std::max<uint64_t>(1, total >> 22));
     const uint64_t per = (total + nslices - 1) / nslices;
     const size_t width = (h_r ? 8 : 0) + (h_c ? 8 : 0);

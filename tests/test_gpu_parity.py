@@ -328,20 +328,29 @@ def test_autotune_bit_identical_and_state_preserved(O):
         check_stream(O, par[i], par[i][3], 1, None, g[i * 20000:(i + 1) * 20000])
 
 
-def test_generate_batch_host_equals_device(O):
-    """End-to-end form: outputs land in host memory; same numbers as the device form."""
+@pytest.mark.parametrize("r_mem,c_mem", [("pinned", "pageable"), ("pinned", "pinned"),
+                                         ("pageable", "pageable")])
+def test_generate_batch_host_equals_device(O, r_mem, c_mem):
+    """End-to-end form: outputs land in host memory (pinned buffers written by the kernel
+    over the link, pageable ones through device slices); same numbers as the device form."""
     ctx = R.Context(32)
     ids, par = seeded(ctx, O, master=22, k=20, rule=R.E_UNIFORM, lo=3, hi=257)
     counts = np.array([1 << 18] * 10 + [12345] * 10, np.uint64)
     total = int(counts.sum())
-    h_r = torch.empty(total, dtype=torch.float64).pin_memory()
-    h_c = np.empty(total, np.uint64)
+    h_r = (torch.empty(total, dtype=torch.float64).pin_memory() if r_mem == "pinned"
+           else np.empty(total, np.float64))
+    h_c = (torch.empty(total, dtype=torch.int64).pin_memory() if c_mem == "pinned"
+           else np.empty(total, np.uint64))
+    before = ctx.transfer_bytes()
     ctx.generate_batch_host(ids, counts, h_r=h_r, h_c=h_c)
-    g = h_r.numpy()
+    after = ctx.transfer_bytes()
+    assert after[1] - before[1] == 16 * total  # device->host bytes of both outputs
+    g = h_r.numpy() if r_mem == "pinned" else h_r
+    gc = h_c.numpy().view(np.uint64) if c_mem == "pinned" else h_c
     off = 0
     for i in range(len(ids)):
         n = int(counts[i])
-        check_stream(O, par[i], par[i][3], 1, h_c[off:off + n], g[off:off + n])
+        check_stream(O, par[i], par[i][3], 1, gc[off:off + n], g[off:off + n])
         off += n
 
 
