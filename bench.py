@@ -299,6 +299,22 @@ def form_plain(R, torch, device, peak_alu, rank) -> dict:
            "e": e, "outputs": "u64+f64",
            "alu_frac": round(_slots([e], [n]) / dt / 1e9 / peak_alu, 4),
            "hbm_GBps": round(16 * n / dt / 1e9, 1)}
+    # The same draw as a plan captured in a CUDA graph (one graph launch per 1e6 outputs).
+    plan = ctx.plan([first], [n])
+    st = torch.cuda.Stream()
+    plan.capture(out_r=orr, out_c=oc, stream=st)
+    for _ in range(3):
+        plan.replay(stream=st)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        plan.replay(stream=st)
+    b.record(st)
+    torch.cuda.synchronize()
+    dt = a.elapsed_time(b) / 1e3 / reps
+    out["graph"] = {"value": round(n / dt / 1e9, 3), "ms_per_call": round(dt * 1e3, 4),
+                    "api": "rsaprng_plan_capture + rsaprng_plan_replay"}
+    plan.close()
     ctx.close()
     return out
 
