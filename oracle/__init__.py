@@ -86,6 +86,7 @@ def _configure(L):
         "or_unit_exact": (dbl, [u64, u64]),
         "or_generate": (i32, [ctypes.c_void_p, pu64, pu64, u64, pu64, pdbl, i32]),
         "or_seek": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
+        "or_seek_parallel": (i32, [ctypes.c_void_p, pu64, pu64, u64]),
         "or_sample": (i32, [ctypes.c_void_p, pu64, pu64, pu64, u64, pu64, pdbl]),
         "or_sample_many": (i32, [u64, pu64, pu64, pu64, pu64, u64, pu64, pu64, pu64,
                                  pu64, pu64, pu64, pdbl]),
@@ -243,6 +244,17 @@ def seek(p, q, a, m0, s0, k, q_mod=Q):
     rc = lib().or_seek(ctypes.byref(P), ctypes.byref(m), ctypes.byref(s), k)
     if rc != 0:
         raise RuntimeError(f"oracle seek failed ({rc})")
+    return m.value, s.value
+
+
+def seek_parallel(p, q, a, m0, s0, k, q_mod=Q):
+    """seek over all host cores: the skip sum split into ranges started by jump-ahead."""
+    P = _Params(p, q, 3, a, q_mod)
+    m = ctypes.c_uint64(m0)
+    s = ctypes.c_uint64(s0)
+    rc = lib().or_seek_parallel(ctypes.byref(P), ctypes.byref(m), ctypes.byref(s), k)
+    if rc != 0:
+        raise RuntimeError(f"oracle seek_parallel failed ({rc})")
     return m.value, s.value
 
 

@@ -448,6 +448,48 @@ int or_seek(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t k)
 }
 
 /*
+ * or_seek over all host cores: the message advances by the sum of the k next
+ * skips (Sec. IV, Eq. pseudoskip), and the sum splits into consecutive
+ * ranges; the range starting after j skips begins from s a^j mod Q (the
+ * skip's jump-ahead, Eq. congruentialgenerator1), so every thread walks its
+ * own range with the skip recurrence and the partial sums are added mod n.
+ */
+int or_seek_parallel(const or_params *P, uint64_t *m_io, uint64_t *s_io, uint64_t k)
+{
+    enum { MAXT = 1024 };
+    const uint64_t n = P->p * P->q, a = P->a, Q = P->Q;
+    const uint64_t s0 = *s_io;
+    if (*m_io >= n || s0 == 0 || s0 >= Q)
+        return OR_ERR_ARG;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    if (nt > MAXT)
+        nt = MAXT;
+    uint64_t part[MAXT];
+    const uint64_t per = (k + (uint64_t)nt - 1) / (uint64_t)nt;
+#pragma omp parallel for schedule(static, 1) num_threads(nt)
+    for (int t = 0; t < nt; t++) {
+        const uint64_t lo = (uint64_t)t * per;
+        const uint64_t hi = (lo + per < k) ? lo + per : k;
+        uint64_t s = or_mulmod(s0, or_powmod(a, lo, Q), Q);
+        uint64_t sum = 0;
+        for (uint64_t j = lo; j < hi; j++) {
+            s = or_skip_next_direct(s, a, Q);
+            sum = or_addmod(sum, s % n, n);
+        }
+        part[t] = sum;
+    }
+    uint64_t m = *m_io;
+    for (int t = 0; t < nt; t++)
+        m = or_addmod(m, part[t], n);
+    *m_io = m;
+    *s_io = or_mulmod(s0, or_powmod(a, k, Q), Q);
+    return OR_OK;
+}
+
+/*
  * Sampled outputs of one instance: for the increasing 1-based output indices
  * ks[0] < ks[1] < ... < ks[nk-1], c_out[j] / r_out[j] receive c_k, r_k with
  * k = ks[j]. The state is advanced by Sec. IV's sums (or_seek) between the

@@ -218,3 +218,12 @@ def test_vector_call_is_the_interleaved_streams():
     for g, (pp, qq, ee, mm) in enumerate(insts):
         cg, _, _, _ = oracle.generate(pp, qq, ee, mm, [1, 99, 1][g], 300, a=int(av[g]))
         np.testing.assert_array_equal(c[g::3], cg)
+
+
+def test_parallel_seek_equals_serial_seek():
+    """The skip sum split over threads (ranges started by jump-ahead) equals the serial walk."""
+    for seed, a in ((800, A), (801, 3), (802, 1)):
+        p, q, _, m0 = _pq(seed)
+        for k in (0, 1, 2, 17, 1000, 123457):
+            s0 = 7 if a != 1 else 99
+            assert oracle.seek_parallel(p, q, a, m0, s0, k) == oracle.seek(p, q, a, m0, s0, k)
