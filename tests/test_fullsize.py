@@ -184,3 +184,30 @@ def test_serving_full_size_sampled(O):
     st = srv.stats()
     assert st["completed"] == n and st["numbers_done"] == int(cnt.sum())
     srv.close()
+
+
+def test_single_stream_beyond_2p32(O):
+    """One stream longer than 2^32 outputs in one call (34 GB of float64): 64-bit positions
+    through planning, the skip-sum pre-pass and the kernels. Checked at the start, across
+    the 2^32 boundary, at the end, and in the end state; the oracle walks the stream."""
+    ctx = R.Context(2)
+    seed = int(workload.instance_seeds(71, 1)[0])
+    p, q, e, ms = O.params_from_seed(seed)
+    m0 = ms % (p * q)
+    i = ctx.create(p, q, e, ms)
+    N = (1 << 32) + 4099
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.generate_f64(i, N, r)
+    torch.cuda.synchronize()
+    _, want, _, _ = O.generate(p, q, e, m0, 1, 5000)
+    assert (bits(r[:5000].cpu().numpy()) == bits(want)).all()
+    k0 = (1 << 32) - 3
+    m, s = O.seek_parallel(p, q, A, m0, 1, k0)
+    _, want, m, s = O.generate(p, q, e, m, s, 6)
+    assert (bits(r[k0:k0 + 6].cpu().numpy()) == bits(want)).all()
+    m, s = O.seek_parallel(p, q, A, m, s, N - (k0 + 6) - 1)
+    _, want, m, s = O.generate(p, q, e, m, s, 1)
+    assert bits(r[N - 1:].cpu().numpy())[0] == bits(want)[0]
+    assert ctx.get_state(i) == (m, s)
+    del r
+    torch.cuda.empty_cache()
