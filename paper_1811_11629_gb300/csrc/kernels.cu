@@ -36,8 +36,20 @@ using tile::block_reduce_mod;
 using tile::sidx;
 using tile::to_unit;
 
-template <int L, int MODEXP, int DIV>
-__global__ void __launch_bounds__(512) k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
+// The default tile (128 threads x 16 outputs on the CRT route) also has an
+// instantiation with a 128-thread, 5-blocks-per-SM launch bound (TB = 128):
+// the compiler then plans its registers for exactly that occupancy (measured
+// 2 % faster than the generic bound). Other tiles use TB = 0 (up to 512).
+constexpr int kTunedThreads = 128;
+template <int L, int MODEXP>
+constexpr bool tuned_tile()
+{
+    return L == 16 && MODEXP == MODEXP_CRT32;
+}
+
+template <int L, int MODEXP, int DIV, int TB>
+__global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
+    k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
                                                   uint32_t nitems, uint32_t *ticket,
                                                   double *__restrict__ out_r,
                                                   u64 *__restrict__ out_c, u64 stride)
@@ -232,12 +244,21 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
 }
 
 template <int L, int MODEXP, int DIV>
+auto gen_kernel(int threads)
+{
+    if constexpr (tuned_tile<L, MODEXP>())
+        if (threads == kTunedThreads)
+            return k_generate<L, MODEXP, DIV, kTunedThreads>;
+    return k_generate<L, MODEXP, DIV, 0>;
+}
+
+template <int L, int MODEXP, int DIV>
 cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                          uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
                          cudaStream_t stream)
 {
     const size_t smem = gen_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = k_generate<L, MODEXP, DIV>;
+    auto kern = gen_kernel<L, MODEXP, DIV>(g.threads);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -250,16 +271,16 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
 }
 
 template <int L, int MODEXP, int DIV>
-const void *gen_kernel_ptr()
+const void *gen_kernel_ptr(int threads)
 {
-    return (const void *)k_generate<L, MODEXP, DIV>;
+    return (const void *)gen_kernel<L, MODEXP, DIV>(threads);
 }
 
-const void *select_kernel(int L, int modexp, int divide)
+const void *select_kernel(int L, int modexp, int divide, int threads)
 {
 #define RSAPRNG_SEL(LL, MM, DD)                                   \
     if (L == LL && modexp == MM && divide == DD)                  \
-        return gen_kernel_ptr<LL, MM, DD>();
+        return gen_kernel_ptr<LL, MM, DD>(threads);
     RSAPRNG_SEL(2, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_SEL(4, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_SEL(8, MODEXP_CRT32, DIVIDE_INT)
@@ -473,7 +494,7 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
 
 int gen_blocks_per_sm(const GenLaunch &g, size_t smem)
 {
-    const void *k = select_kernel(g.L, g.modexp, g.divide);
+    const void *k = select_kernel(g.L, g.modexp, g.divide, g.threads);
     if (!k)
         return 0;
     if (smem > 48 * 1024)
