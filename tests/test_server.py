@@ -123,3 +123,36 @@ def test_server_replay_open_loop(O):
     assert st["completed"] == n and st["numbers_done"] == int(cnt.sum())
     assert (lat > 0).all() and st["p99_ms"] >= st["p50_ms"] > 0
     srv.close()
+
+
+def test_server_serves_every_mode(O):
+    """Constant-skip and CRT-exponent instances through the server, mixed with ordinary ones,
+    under the exact-rational reading: every request equals its instance's next numbers."""
+    import math
+
+    ctx = R.Context(16, rounding=R._lib.ROUND_EXACT)
+    p0, q0, e0, ms0 = O.params_from_seed(int(workload.instance_seeds(33, 1)[0]))
+    i0 = ctx.create_ex(p0, q0, e0, 1, ms0 % (p0 * q0), 31337)  # constant skip
+    p1, q1, _, ms1 = O.params_from_seed(int(workload.instance_seeds(34, 1)[0]))
+    ep = next(x for x in range(5, 99, 2) if math.gcd(x, p1 - 1) == 1)
+    eq = next(x for x in range(ep + 2, 199, 2) if math.gcd(x, q1 - 1) == 1)
+    i1 = ctx.create_crt(p1, q1, ep, eq, R.DEFAULT_ROOT, ms1 % (p1 * q1), 1)
+    p2, q2, e2, ms2 = O.params_from_seed(int(workload.instance_seeds(35, 1)[0]))
+    i2 = ctx.create(p2, q2, e2, ms2)
+    srv = R.Server(ctx, out_budget_bytes=16 << 20, nstreams=2)
+    reqs = [(i0, 70001), (i1, 5000), (i2, 123457), (i0, 3), (i1, 99999), (i2, 1)]
+    tickets = [srv.submit(i, n) for i, n in reqs]
+    got = {}
+    for (i, n), t in zip(reqs, tickets):
+        srv.wait(t, timeout_s=120)
+        got.setdefault(i, []).append(srv.result(t).cpu().numpy())
+        srv.release(t)
+    srv.close()
+    spec = {i0: (p0, q0, e0, ms0 % (p0 * q0), 31337, 1, 0),
+            i1: (p1, q1, ep, ms1 % (p1 * q1), 1, R.DEFAULT_ROOT, eq),
+            i2: (p2, q2, e2, ms2 % (p2 * q2), 1, R.DEFAULT_ROOT, 0)}
+    for i, (p, q, e, m0, s0, a, eqq) in spec.items():
+        seq = np.concatenate(got[i])
+        c, _, _, _ = O.generate(p, q, e, m0, s0, len(seq), a=a, eq=eqq)
+        want = O.unit_exact_many(c, p * q)
+        assert (seq.view(np.uint64) == want.view(np.uint64)).all()
