@@ -9,19 +9,10 @@
 #include "../../include/rsaprng.h"
 #include "host_params.hpp"
 #include "kernels.cuh"
+#include "plan_core.hpp"
 
 namespace rsaprng {
 
-// Work lists of one launch sequence, built on the host.
-struct HostPlan {
-    std::vector<WorkItem> items;
-    std::vector<PrepChunk> chunks;
-    std::vector<PrepGroup> groups;
-    uint64_t numbers = 0;
-    uint64_t stride = 1;  // element distance between consecutive outputs of a request
-    std::vector<VecGroup> vecs;  // stride > 1: blocks' units of the vector kernel
-    int vec_ts = 0;              // threads per instance in the vector kernel
-};
 
 // The same lists in device memory (one allocation) plus the skip-sum scratch.
 struct DevPlan {
@@ -77,7 +68,6 @@ struct rsaprng_ctx {
 
 namespace rsaprng {
 
-int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 DeviceTables ctx_tables(rsaprng_ctx *c);
 GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems, bool want_r,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "host_params.hpp"
+#include "work.hpp"
 
 namespace rsaprng {
 
@@ -15,40 +16,6 @@ constexpr int kMaxThreads = 1024;
 constexpr int kMaxL = 16;
 constexpr int kMaxTile = kMaxThreads * kMaxL;
 constexpr int kPowLinRow = kMaxTile + 1;
-
-// One unit of work for the generation kernel: `count` consecutive outputs of
-// instance `inst` written from element `out_off` of the output arrays (one
-// element apart, or a launch-wide stride apart for the interleaved order),
-// starting from the state (m0, s0) before the first output.
-enum : uint32_t {
-    WI_FROM_STATE = 1u,  // take (m0, s0) from the instance state table
-    WI_WRITEBACK = 2u,   // store the state after the last output
-};
-struct WorkItem {
-    uint32_t inst;
-    uint32_t flags;
-    uint64_t count;
-    uint64_t out_off;
-    uint64_t m0, s0;
-};
-static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
-
-// Chunks of one instance's stream whose start state comes from the skip-sum
-// pass: chunk i of the list covers outputs offset+1 .. offset+len of the
-// instance's stream in this launch and fills work item `item`.
-struct PrepChunk {
-    uint32_t inst;
-    uint32_t item;
-    uint64_t offset;
-    uint64_t len;
-};
-// A run of consecutive PrepChunk entries (in stream order) of one instance.
-struct PrepGroup {
-    uint32_t inst;
-    uint32_t first;
-    uint32_t count;
-    uint32_t pad;
-};
 
 enum Modexp { MODEXP_CRT32 = 1, MODEXP_MONT64 = 2 };
 // DIVIDE_HYBRID sends three of every four outputs of a thread through the
@@ -79,18 +46,7 @@ struct GenLaunch {
 // Shared memory bytes the generation kernel needs for a tile.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
 
-// The interleaved (vector) order: a block takes up to G = threads / TS work
-// items that cover the same positions of consecutive instances of a vector
-// (items first .. first+count-1, output elements one apart).
-struct VecGroup {
-    uint32_t first;
-    uint32_t count;
-};
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c);
-// Threads per instance (TS) for a block of `threads` and a vector of `stride`
-// instances: G = threads / TS instances per block, the smallest power of two
-// >= stride between threads / 32 and threads / 4.
-int vec_threads_per_instance(int threads, uint64_t stride);
 cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                                 const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
                                 double *out_r, uint64_t *out_c, int TS, cudaStream_t stream);

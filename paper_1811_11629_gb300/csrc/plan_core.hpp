@@ -1,0 +1,57 @@
+// The host planner's interface (plain C++, no CUDA types), shared by the
+// library's runtime and the host-only planner tests.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "host_params.hpp"
+#include "work.hpp"
+
+namespace rsaprng {
+
+// Work lists of one launch sequence, built on the host.
+struct HostPlan {
+    std::vector<WorkItem> items;
+    std::vector<PrepChunk> chunks;
+    std::vector<PrepGroup> groups;
+    uint64_t numbers = 0;
+    uint64_t stride = 1;  // element distance between consecutive outputs of a request
+    std::vector<VecGroup> vecs;  // stride > 1: blocks' units of the vector kernel
+    int vec_ts = 0;              // threads per instance in the vector kernel
+};
+
+// Shape of the generation launch the pieces are sized for.
+struct PlanGeometry {
+    uint64_t threads;  // threads per block
+    uint64_t L;        // outputs per thread per tile
+    uint64_t grid;     // resident blocks
+};
+
+// Error reporting (defined by the runtime; returns code).
+int fail(int code, const char *fmt, ...);
+
+// Cost of one output of an instance with exponent e, in Montgomery-product
+// units plus a fixed share (the planner's balance weight).
+uint64_t cost_per_number(uint32_t e);
+
+// Threads per instance (TS) of the vector kernel for a block of `threads`
+// and a vector of `stride` instances: G = threads / TS instances per block,
+// the smallest power of two >= stride between threads / 32 and threads / 4.
+int vec_threads_per_instance(int threads, uint64_t stride);
+
+// Cuts requests (instance ids[i], counts[i] outputs, written from element
+// offsets[i], consecutive outputs `stride` elements apart) into work items:
+// requests of one instance continue its stream in array order; a stream is
+// cut into pieces of whole tiles (multiples of `tuple` outputs too) so that
+// the work spreads over geo.grid blocks, at most `chunk` outputs each (0: no
+// cap; with tuple > 1 the cap is rounded down to whole units of tile x tuple,
+// at least one unit); pieces after an instance's first get their start state from the
+// skip-sum pre-pass (chunks, groups). Items are ordered longest first, or by
+// position when stride > 1 (then grouped into VecGroups). params has ninst
+// entries. Errors: RSAPRNG_ERR_ID, RSAPRNG_ERR_ARG.
+int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const PlanGeometry &geo,
+                    uint64_t nreq, const uint32_t *ids, const uint64_t *counts,
+                    const uint64_t *offsets, uint64_t chunk, HostPlan &hp, uint64_t tuple = 1,
+                    uint64_t stride = 1);
+
+}  // namespace rsaprng

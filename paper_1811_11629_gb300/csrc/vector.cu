@@ -211,14 +211,6 @@ size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
     return gen_smem_bytes(threads, L, want_r, want_c);  // the same padded slots
 }
 
-int vec_threads_per_instance(int threads, uint64_t stride)
-{
-    int G = threads / 4;  // at most: four threads per instance
-    while (G > threads / 32 && (uint64_t)(G / 2) >= stride)
-        G /= 2;
-    return threads / G;
-}
-
 cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                                 const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
                                 double *out_r, uint64_t *out_c, int TS, cudaStream_t stream)

@@ -1,0 +1,255 @@
+// Host-only checks of the planner (plan_core.cpp) on random request sets and
+// launch geometries. Invariants checked for every plan:
+//  1. every request's outputs are covered exactly once, at the elements
+//     offsets[i] + k * stride, and the outputs of one instance follow its
+//     stream (requests of an instance continue one another in array order);
+//  2. an instance cut into one piece reads and writes back the state table;
+//     cut into several, only its last piece writes back, and its pieces are
+//     listed as skip-sum chunks (the last with length 0) in stream order;
+//  3. pieces start on tiles (and on multiples of the tuple), respect the
+//     chunk cap, and are ordered longest first (or by position for stride > 1);
+//  4. vector groups partition the items into runs of neighbours;
+//  5. unknown ids and CRT exponents on the 64-bit route are refused.
+// Exit status 0 when every case passes.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <random>
+#include <vector>
+
+#include "../include/rsaprng.h"
+#include "../paper_1811_11629_gb300/csrc/plan_core.hpp"
+
+namespace rsaprng {
+int fail(int code, const char *, ...) { return code; }
+}  // namespace rsaprng
+
+using namespace rsaprng;
+
+static int failures = 0;
+#define CHECK(cond, ...)                                                    \
+    do {                                                                    \
+        if (!(cond)) {                                                      \
+            if (failures < 20) {                                            \
+                std::printf("case %d: %s: ", case_no, #cond);               \
+                std::printf(__VA_ARGS__);                                   \
+                std::printf("\n");                                          \
+            }                                                               \
+            failures++;                                                     \
+            return;                                                         \
+        }                                                                   \
+    } while (0)
+
+static int case_no = 0;
+
+static void check_case(std::mt19937_64 &rng, bool vector_order)
+{
+    case_no++;
+    const uint64_t threads_opts[] = {64, 128, 256, 512}, L_opts[] = {2, 4, 8, 16};
+    PlanGeometry geo{threads_opts[rng() % 4], L_opts[rng() % 4], 1 + rng() % 1200};
+    const uint64_t ninst = 1 + rng() % 40;
+    std::vector<InstParams> params(ninst);
+    for (auto &p : params) {
+        p.e = (uint32_t)(3 + 2 * (rng() % 40000));
+        p.eq = (rng() % 5 == 0) ? (uint32_t)(3 + 2 * (rng() % 300)) : p.e;
+    }
+    std::vector<uint32_t> ids;
+    std::vector<uint64_t> counts, offsets;
+    uint64_t stride = 1, tuple = 1;
+    const uint64_t scale = (rng() % 3 == 0) ? 200000 : 3000;
+    if (vector_order) {
+        // vectors of Mv distinct instances, all of length N, k-major
+        const uint64_t Mv = 1 + rng() % std::min<uint64_t>(ninst, 40);
+        const uint64_t groups = std::max<uint64_t>(1, ninst / Mv);
+        const uint64_t N = rng() % scale;
+        stride = Mv;
+        std::vector<uint32_t> perm(ninst);
+        for (uint32_t i = 0; i < ninst; i++)
+            perm[i] = i;
+        if (rng() % 2)
+            std::shuffle(perm.begin(), perm.end(), rng);
+        for (uint64_t g = 0; g < groups; g++)
+            for (uint64_t j = 0; j < Mv; j++) {
+                ids.push_back(perm[g * Mv + j]);
+                counts.push_back(N);
+                offsets.push_back(g * N * Mv + j);
+            }
+    } else {
+        const uint64_t nreq = 1 + rng() % 60;
+        tuple = (rng() % 4 == 0) ? 1 + rng() % 6 : 1;
+        uint64_t off = 0;
+        for (uint64_t i = 0; i < nreq; i++) {
+            // histogram plans (tuple > 1) take one request per instance
+            uint32_t id = (uint32_t)(rng() % ninst);
+            if (tuple > 1) {
+                if (i >= ninst)
+                    break;
+                id = (uint32_t)i;
+            }
+            const uint64_t c = (rng() % 7 == 0) ? 0 : rng() % scale;
+            ids.push_back(id);
+            counts.push_back(c);
+            offsets.push_back(off);
+            off += c;
+        }
+    }
+    const uint64_t chunk_opts[] = {0, 1ULL << 12, 1ULL << 16, 5000, 1ULL << 18};
+    const uint64_t chunk = chunk_opts[rng() % 5];
+    const int modexp = (rng() % 4 == 0) ? RSAPRNG_MODEXP_MONT64 : RSAPRNG_MODEXP_CRT32;
+    HostPlan hp;
+    const int rc = build_plan_core(params.data(), ninst, modexp, geo, ids.size(), ids.data(),
+                                   counts.data(), offsets.data(), chunk, hp, tuple, stride);
+    bool split_e = false;
+    for (uint32_t id : ids)
+        split_e |= params[id].e != params[id].eq;
+    if (split_e && modexp == RSAPRNG_MODEXP_MONT64) {
+        CHECK(rc == RSAPRNG_ERR_ARG, "rc=%d", rc);
+        return;
+    }
+    CHECK(rc == RSAPRNG_OK, "rc=%d", rc);
+
+    // 1. coverage and stream order: stream position -> element, per instance
+    std::map<uint32_t, std::vector<uint64_t>> want;  // instance -> element of each position
+    uint64_t total = 0;
+    for (size_t i = 0; i < ids.size(); i++) {
+        auto &v = want[ids[i]];
+        for (uint64_t k = 0; k < counts[i]; k++)
+            v.push_back(offsets[i] + k * stride);
+        total += counts[i];
+    }
+    CHECK(hp.numbers == total, "numbers %llu != %llu", (unsigned long long)hp.numbers,
+          (unsigned long long)total);
+    std::map<uint32_t, std::vector<uint64_t>> got;  // instance -> (position -> element)
+    std::map<uint32_t, std::vector<size_t>> items_of;
+    uint64_t sum_items = 0;
+    for (size_t k = 0; k < hp.items.size(); k++) {
+        items_of[hp.items[k].inst].push_back(k);
+        sum_items += hp.items[k].count;
+        CHECK(hp.items[k].count > 0, "empty item");
+    }
+    CHECK(sum_items == total, "items cover %llu of %llu", (unsigned long long)sum_items,
+          (unsigned long long)total);
+    // chunks give each multi-piece item its stream offset
+    std::vector<int64_t> item_off(hp.items.size(), -1);
+    for (const auto &g : hp.groups) {
+        uint64_t expect = 0;
+        for (uint32_t j = 0; j < g.count; j++) {
+            const PrepChunk &c = hp.chunks[g.first + j];
+            CHECK(c.inst == g.inst && c.item < hp.items.size(), "chunk of another instance");
+            const WorkItem &w = hp.items[c.item];
+            CHECK(w.inst == g.inst, "chunk item of another instance");
+            CHECK(c.offset == expect, "chunk offsets not contiguous");
+            const bool last = j + 1 == g.count;
+            CHECK(c.len == (last ? 0 : w.count), "chunk length");
+            CHECK(!(w.flags & WI_FROM_STATE), "piece after the first reads the state");
+            CHECK(((w.flags & WI_WRITEBACK) != 0) == last, "write-back not on the last piece");
+            item_off[c.item] = (int64_t)c.offset;
+            expect += w.count;
+        }
+    }
+    for (auto &kv : items_of) {
+        const uint32_t inst = kv.first;
+        auto &v = got[inst];
+        v.assign(want[inst].size(), ~0ULL);
+        for (size_t k : kv.second) {
+            const WorkItem &w = hp.items[k];
+            uint64_t base = 0;
+            if (item_off[k] < 0) {
+                // 2. a single piece: reads and writes the state table
+                CHECK(kv.second.size() == 1, "several items without chunks");
+                CHECK(w.flags == (WI_FROM_STATE | WI_WRITEBACK), "single piece flags %u", w.flags);
+            } else {
+                base = (uint64_t)item_off[k];
+            }
+            for (uint64_t j = 0; j < w.count; j++) {
+                CHECK(base + j < v.size(), "position beyond the instance's outputs");
+                CHECK(v[base + j] == ~0ULL, "position covered twice");
+                v[base + j] = w.out_off + j * stride;
+            }
+            // 3. pieces start on tiles (and tuples); all but an instance's last
+            // piece hold whole tiles and respect the chunk cap
+            if (item_off[k] > 0 && tuple > 1)
+                CHECK(base % tuple == 0, "piece off a tuple boundary");
+            // with tuples the cap is whole units of tile x tuple, at least one
+            const uint64_t unit = geo.threads * geo.L * tuple;
+            const uint64_t cap = tuple > 1 ? std::max(unit, chunk / unit * unit) : chunk;
+            if (chunk && w.count > cap)
+                CHECK(false, "piece of %llu over the chunk cap %llu (tuple %llu stride %llu)",
+                      (unsigned long long)w.count, (unsigned long long)cap,
+                      (unsigned long long)tuple, (unsigned long long)stride);
+        }
+        CHECK(v == want[inst], "instance %u: elements differ from the requests", inst);
+    }
+    // 3. order of the items
+    for (size_t k = 1; k < hp.items.size(); k++) {
+        if (stride == 1) {
+            auto cost = [&](const WorkItem &w) {
+                return w.count *
+                       cost_per_number(std::max(params[w.inst].e, params[w.inst].eq));
+            };
+            CHECK(cost(hp.items[k - 1]) >= cost(hp.items[k]), "not longest first");
+        } else {
+            const uint64_t a = item_off[k - 1] < 0 ? 0 : (uint64_t)item_off[k - 1];
+            const uint64_t b = item_off[k] < 0 ? 0 : (uint64_t)item_off[k];
+            CHECK(a <= b, "vector order not by position");
+        }
+    }
+    // 4. vector groups
+    if (stride > 1) {
+        const uint32_t G = (uint32_t)(geo.threads / (uint64_t)hp.vec_ts);
+        CHECK(hp.vec_ts >= 1 && geo.threads % hp.vec_ts == 0 && hp.vec_ts <= 32 && hp.vec_ts >= 4,
+              "threads per instance %d", hp.vec_ts);
+        uint32_t next = 0;
+        for (const auto &g : hp.vecs) {
+            CHECK(g.first == next && g.count >= 1 && g.count <= G, "group layout");
+            for (uint32_t j = 1; j < g.count; j++) {
+                const WorkItem &a = hp.items[g.first + j - 1], &b = hp.items[g.first + j];
+                CHECK(b.count == a.count && b.out_off == a.out_off + 1, "group members not neighbours");
+            }
+            next += g.count;
+        }
+        CHECK(next == hp.items.size(), "groups cover %u of %zu items", next, hp.items.size());
+    } else {
+        CHECK(hp.vecs.empty(), "vector groups in a contiguous plan");
+    }
+}
+
+int main(int argc, char **argv)
+{
+    const int cases = argc > 1 ? std::atoi(argv[1]) : 3000;
+    std::mt19937_64 rng(20261203);
+    for (int i = 0; i < cases; i++)
+        check_case(rng, i % 3 == 2);
+    // 5. refusals
+    {
+        case_no++;
+        std::vector<InstParams> params(2);
+        params[0].e = params[0].eq = 5;
+        params[1].e = 5;
+        params[1].eq = 7;
+        const PlanGeometry geo{128, 16, 760};
+        HostPlan hp;
+        const uint32_t bad[1] = {2};
+        const uint64_t cnt[1] = {10}, off[1] = {0};
+        int rc = build_plan_core(params.data(), 2, RSAPRNG_MODEXP_CRT32, geo, 1, bad, cnt, off, 0, hp);
+        if (rc != RSAPRNG_ERR_ID) {
+            std::printf("unknown id accepted (rc=%d)\n", rc);
+            failures++;
+        }
+        const uint32_t split[1] = {1};
+        rc = build_plan_core(params.data(), 2, RSAPRNG_MODEXP_MONT64, geo, 1, split, cnt, off, 0, hp);
+        if (rc != RSAPRNG_ERR_ARG) {
+            std::printf("CRT exponents accepted on the 64-bit route (rc=%d)\n", rc);
+            failures++;
+        }
+        rc = build_plan_core(params.data(), 2, RSAPRNG_MODEXP_CRT32, geo, 1, split, cnt, off, 0, hp);
+        if (rc != RSAPRNG_OK) {
+            std::printf("CRT exponents refused on the CRT route (rc=%d)\n", rc);
+            failures++;
+        }
+    }
+    std::printf("%d cases, %d failures\n", case_no, failures);
+    return failures ? 1 : 0;
+}

@@ -1,0 +1,43 @@
+"""The host planner (plan_core.cpp) on random request sets and launch geometries, built
+with the host compiler and run without a GPU (invariants listed in plan_check.cpp), and
+planted mistakes in a copy of the planner that the checks must catch."""
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CORE = os.path.join(ROOT, "paper_1811_11629_gb300", "csrc", "plan_core.cpp")
+HARNESS = os.path.join(ROOT, "tests", "plan_check.cpp")
+
+
+def build_and_run(tmp_path, core_src, cases=3000):
+    exe = tmp_path / "plan_check"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.dirname(CORE), "-o", str(exe),
+                    HARNESS, str(core_src)], check=True)
+    return subprocess.run([str(exe), str(cases)], capture_output=True, text=True, timeout=600)
+
+
+def test_planner_invariants(tmp_path):
+    out = build_and_run(tmp_path, CORE)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    assert "0 failures" in out.stdout
+
+
+MUTANTS = {
+    "stride_ignored": ("out += len * stride;", "out += len;"),
+    "last_chunk_summed": ("last ? 0 : pieces[k].len", "pieces[k].len"),
+    "shortest_first": ("return item_cost[x] > item_cost[y];", "return item_cost[x] < item_cost[y];"),
+    "groups_of_strangers": ("&&\n                   hp.items[j].out_off == hp.items[j - 1].out_off + 1)", ")"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_planner_mistake_is_caught(tmp_path, name):
+    before, after = MUTANTS[name]
+    src = open(CORE).read()
+    assert src.count(before) == 1, name
+    mutated = tmp_path / "plan_core.cpp"
+    mutated.write_text(src.replace(before, after))
+    out = build_and_run(tmp_path, mutated, cases=500)
+    assert out.returncode != 0, f"the planner checks miss the planted mistake {name}"
