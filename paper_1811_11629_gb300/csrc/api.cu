@@ -267,7 +267,8 @@ static GenLaunch hist_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t
 }
 
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
-                uint64_t *d_c, cudaStream_t stream, uint64_t *launches, const HistArgs *hist)
+                uint64_t *d_c, cudaStream_t stream, uint64_t *launches, const HistArgs *hist,
+                bool fresh)
 {
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
@@ -289,7 +290,7 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
                                          &dp.occupancy);
         g.stride = dp.stride;
         dp.last = g;
-        if (g.persistent) {
+        if (g.persistent && !fresh) {
             if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
                 return cuda_fail(e, "ticket reset");
         }
@@ -763,7 +764,7 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
         return rc;
     if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
         return rc;
-    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr);
+    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr, nullptr, true);
     cudaEventRecord(slot->done, st);
     slot->used = true;
     return rc;
@@ -801,7 +802,7 @@ int rsaprng_generate_interleaved(rsaprng_ctx *c, uint64_t ngroups, uint32_t Mv,
         return rc;
     if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
         return rc;
-    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr);
+    rc = launch_plan(c, c->cfg, slot->plan, d_r, d_c, st, nullptr, nullptr, true);
     cudaEventRecord(slot->done, st);
     slot->used = true;
     return rc;
@@ -846,7 +847,7 @@ int rsaprng_histogram(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
     if ((rc = upload_plan(c, hp, slot->plan, st)) != RSAPRNG_OK)
         return rc;
     const HistArgs h{(unsigned long long *)d_hist, d, D, source == RSAPRNG_HIST_LOW ? 1u : 0u, 0u};
-    rc = launch_plan(c, c->cfg, slot->plan, nullptr, nullptr, st, nullptr, &h);
+    rc = launch_plan(c, c->cfg, slot->plan, nullptr, nullptr, st, nullptr, &h, true);
     cudaEventRecord(slot->done, st);
     slot->used = true;
     return rc;

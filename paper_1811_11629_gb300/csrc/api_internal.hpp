@@ -80,10 +80,13 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
                uint64_t tuple = 1, uint64_t stride = 1);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
 // Launches the pre-pass and the generation kernel, or the histogram
-// consumer instead of the generation kernel when hist is given.
+// consumer instead of the generation kernel when hist is given. fresh: the
+// plan was uploaded for this launch alone, so its work-queue counter is still
+// the zero the upload wrote (a plan launched again, or captured in a graph,
+// resets it on the stream).
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
                 uint64_t *d_c, cudaStream_t stream, uint64_t *launches,
-                const HistArgs *hist = nullptr);
+                const HistArgs *hist = nullptr, bool fresh = false);
 void free_devplan(DevPlan &dp);
 int scratch_slot(rsaprng_ctx *c, ScratchSlot **out);
 

@@ -100,6 +100,8 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         uint64_t len = npieces > 1 ? (total + npieces - 1) / npieces : total;
         len = (len + tile - 1) / tile * tile;
         const uint64_t cut = std::max<uint64_t>(1, std::min(chunk, len));
+        hp.items.reserve(hp.items.size() + total / cut + (g1 - g0));
+        hp.chunks.reserve(hp.chunks.size() + total / cut + (g1 - g0));
         uint64_t off = 0;
         for (uint64_t k = g0; k < g1; k++) {
             const uint64_t r = order[k];
@@ -143,23 +145,29 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     // interleaved order (stride > 1) the outputs of different instances at
     // the same position share memory sectors: pieces are ordered by position
     // instead, so those writes happen side by side and merge in L2.
-    std::vector<uint32_t> perm(hp.items.size()), where(hp.items.size());
-    for (size_t i = 0; i < perm.size(); i++)
-        perm[i] = (uint32_t)i;
-    if (stride > 1)
-        std::stable_sort(perm.begin(), perm.end(),
-                         [&](uint32_t x, uint32_t y) { return item_pos[x] < item_pos[y]; });
-    else
-        std::stable_sort(perm.begin(), perm.end(),
-                         [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
-    std::vector<WorkItem> sorted(hp.items.size());
-    for (size_t i = 0; i < perm.size(); i++) {
-        sorted[i] = hp.items[perm[i]];
-        where[perm[i]] = (uint32_t)i;
+    const bool ordered =
+        stride > 1 ? std::is_sorted(item_pos.begin(), item_pos.end())
+                   : std::is_sorted(item_cost.begin(), item_cost.end(),
+                                    [](uint64_t x, uint64_t y) { return x > y; });
+    if (!ordered) {
+        std::vector<uint32_t> perm(hp.items.size()), where(hp.items.size());
+        for (size_t i = 0; i < perm.size(); i++)
+            perm[i] = (uint32_t)i;
+        if (stride > 1)
+            std::stable_sort(perm.begin(), perm.end(),
+                             [&](uint32_t x, uint32_t y) { return item_pos[x] < item_pos[y]; });
+        else
+            std::stable_sort(perm.begin(), perm.end(),
+                             [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
+        std::vector<WorkItem> sorted(hp.items.size());
+        for (size_t i = 0; i < perm.size(); i++) {
+            sorted[i] = hp.items[perm[i]];
+            where[perm[i]] = (uint32_t)i;
+        }
+        hp.items.swap(sorted);
+        for (auto &pc : hp.chunks)
+            pc.item = where[pc.item];
     }
-    hp.items.swap(sorted);
-    for (auto &pc : hp.chunks)
-        pc.item = where[pc.item];
     if (stride > 1) {
         // Units of the vector kernel: up to G items in a row with the same
         // length whose outputs are neighbours (consecutive instances of a

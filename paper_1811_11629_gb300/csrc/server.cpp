@@ -294,7 +294,8 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     if (rc == RSAPRNG_OK)
         rc = upload_plan(S->ctx, hp, sl.plan, sl.stream);
     if (rc == RSAPRNG_OK)
-        rc = launch_plan(S->ctx, S->ctx->cfg, sl.plan, S->d_arena, nullptr, sl.stream, nullptr);
+        rc = launch_plan(S->ctx, S->ctx->cfg, sl.plan, S->d_arena, nullptr, sl.stream, nullptr,
+                         nullptr, true);
     cudaEventRecord(sl.done, sl.stream);
     sl.t_launch = now_s();
     sl.busy = true;
