@@ -100,8 +100,6 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         uint64_t len = npieces > 1 ? (total + npieces - 1) / npieces : total;
         len = (len + tile - 1) / tile * tile;
         const uint64_t cut = std::max<uint64_t>(1, std::min(chunk, len));
-        hp.items.reserve(hp.items.size() + total / cut + (g1 - g0));
-        hp.chunks.reserve(hp.chunks.size() + total / cut + (g1 - g0));
         uint64_t off = 0;
         for (uint64_t k = g0; k < g1; k++) {
             const uint64_t r = order[k];

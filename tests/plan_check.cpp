@@ -12,11 +12,13 @@
 //  5. unknown ids and CRT exponents on the 64-bit route are refused.
 // Exit status 0 when every case passes.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "../include/rsaprng.h"
@@ -216,8 +218,33 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
     }
 }
 
+// Planning time for many instances (the split workload's shape): the
+// planner must stay linear in the number of pieces.
+static double plan_time_ms(int k, uint64_t stride)
+{
+    std::vector<InstParams> P(k);
+    for (auto &p : P)
+        p.e = p.eq = 3;
+    std::vector<uint32_t> ids(k);
+    std::vector<uint64_t> cnt(k, 65536), off(k);
+    for (int i = 0; i < k; i++) {
+        ids[i] = (uint32_t)i;
+        off[i] = stride == 1 ? (uint64_t)i * 65536 : (uint64_t)(i / 32) * 65536 * 32 + (i % 32);
+    }
+    const PlanGeometry geo{128, 16, 760};
+    HostPlan hp;
+    const auto t0 = std::chrono::steady_clock::now();
+    build_plan_core(P.data(), k, RSAPRNG_MODEXP_CRT32, geo, k, ids.data(), cnt.data(), off.data(),
+                    0, hp, 1, stride);
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 int main(int argc, char **argv)
 {
+    if (argc > 1 && std::string(argv[1]) == "--time") {
+        std::printf("plan_ms %.2f %.2f\n", plan_time_ms(32768, 1), plan_time_ms(32768, 32));
+        return 0;
+    }
     const int cases = argc > 1 ? std::atoi(argv[1]) : 3000;
     std::mt19937_64 rng(20261203);
     for (int i = 0; i < cases; i++)

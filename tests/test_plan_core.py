@@ -24,6 +24,17 @@ def test_planner_invariants(tmp_path):
     assert "0 failures" in out.stdout
 
 
+def test_planner_time_is_linear(tmp_path):
+    """32768 instances (the split workload's shape) plan in well under a second; a planner
+    that grows its lists per instance instead of geometrically takes seconds here."""
+    exe = tmp_path / "plan_check"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.dirname(CORE), "-o", str(exe),
+                    HARNESS, CORE], check=True)
+    out = subprocess.run([str(exe), "--time"], capture_output=True, text=True, timeout=300)
+    ms = [float(x) for x in out.stdout.split()[1:3]]
+    assert max(ms) < 1000.0, out.stdout
+
+
 MUTANTS = {
     "stride_ignored": ("out += len * stride;", "out += len;"),
     "last_chunk_summed": ("last ? 0 : pieces[k].len", "pieces[k].len"),
