@@ -329,7 +329,7 @@ def form_batched(R, torch, device, peak_alu, rank) -> dict:
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
                               cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
-    tuned = ctx.autotune(ids[:2000], lens[:2000], reps=1)
+    tuned = ctx.autotune(ids[:2000], lens[:2000], reps=3)
     plan = ctx.plan(ids, lens)
     total = int(lens.sum())
     out = torch.empty(total, dtype=torch.float64, device="cuda")
@@ -394,7 +394,7 @@ def form_fused(R, torch, device, peak_alu, rank) -> dict:
     return out
 
 
-def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 256) -> dict:
+def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> dict:
     """The vectorised call of Sec. VI: a slice of the split workload (parents x 32 substreams
     x 2^16, e = 3 or the next valid odd, u64 + f64), every parent's k-major vector in one
     call; the substream-major batch over the same children is timed beside it."""
@@ -447,7 +447,7 @@ def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dic
     pick = first + workload.uniform_indices(61, nreq, k)
     cnt = workload.loguniform_counts(62, nreq, lo=16, hi=1 << 24)
     # tune the tiling on a sample of the request mix (the instance states are restored)
-    tuned = ctx.autotune(pick[:512], np.minimum(cnt[:512], 1 << 20), reps=1)
+    tuned = ctx.autotune(pick[:512], np.minimum(cnt[:512], 1 << 20), reps=3)
     srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
     mean_cnt = float(cnt.mean())
     # capacity: all requests at once (arrival 0), the server batching freely
