@@ -107,7 +107,9 @@ typedef struct {
     int32_t modexp;             /* RSAPRNG_MODEXP_* */
     int32_t divide;             /* RSAPRNG_DIVIDE_* */
     int32_t threads_per_block;  /* 64, 128, 256 or 512 */
-    int32_t numbers_per_thread; /* 2, 4, 8 or 16 (the 64-bit route uses 8 for 16) */
+    int32_t numbers_per_thread; /* 2, 4, 8 or 16 (the 64-bit route uses 8 for 16; the
+                                   interleaved call uses 8 for 16 on the CRT route in
+                                   blocks of 128 threads, its tuned tile) */
     int32_t blocks_per_sm;      /* persistent-launch occupancy target */
     uint64_t chunk;             /* maximum numbers per chunk of a long stream
                                    (multiple of threads_per_block*numbers_per_thread);

@@ -143,9 +143,11 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
                uint64_t tuple, uint64_t stride)
 {
-    // The pieces are sized for the generation kernel's resident blocks.
+    // The pieces are sized for the generation kernel's resident blocks, in
+    // tiles of the kernel that runs the plan.
     const GenLaunch full = ctx_launch(c, cfg, ~0ULL, true, false);
-    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid};
+    const int L = stride > 1 ? vec_numbers_per_thread(full.L, full.modexp, full.threads) : full.L;
+    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)L, (uint64_t)full.grid};
     return build_plan_core(c->h_params.data(), c->count, cfg.modexp, geo, nreq, ids, counts,
                            offsets, chunk, hp, tuple, stride);
 }
@@ -240,6 +242,7 @@ static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t 
                             bool want_c)
 {
     GenLaunch g = ctx_launch(c, cfg, nvecs, want_r, want_c);
+    g.L = vec_numbers_per_thread(g.L, g.modexp, g.threads);
     int occ = vec_blocks_per_sm(g, vec_smem_bytes(g.threads, g.L, want_r, want_c));
     if (occ < 1)
         occ = 1;

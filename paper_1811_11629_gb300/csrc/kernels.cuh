@@ -47,6 +47,9 @@ struct GenLaunch {
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c);
+// Numbers per thread the vector kernel uses for a configured L: the tuned
+// tile where it applies, else L itself.
+int vec_numbers_per_thread(int L, int modexp, int threads);
 cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                                 const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
                                 double *out_r, uint64_t *out_c, int TS, cudaStream_t stream);

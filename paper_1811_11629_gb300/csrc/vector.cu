@@ -26,17 +26,20 @@ using dev::mulmodQ;
 using tile::sidx;
 using tile::to_unit;
 
-template <int L, int MODEXP, int DIV>
-__global__ void __launch_bounds__(512)
+// TB > 0: the tuned instance for blocks of exactly TB threads, bounded to
+// five resident blocks per SM.
+template <int L, int MODEXP, int DIV, int TB>
+__global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     k_generate_vec(DeviceTables tab, const WorkItem *__restrict__ items,
                    const VecGroup *__restrict__ vecs, uint32_t nvecs, uint32_t *ticket,
                    double *__restrict__ out_r, u64 *__restrict__ out_c, u64 stride, int TS)
 {
     extern __shared__ u64 smem[];
     __shared__ uint32_t sh_item;
-    const int T = blockDim.x, t = threadIdx.x;
+    const int T = TB ? TB : (int)blockDim.x, t = threadIdx.x;
     const int tsh = __ffs(TS) - 1, G = T >> tsh, gsh = __ffs(G) - 1;  // both powers of two
     const int seg = t >> tsh, lt = t & (TS - 1);
+    const int wcol = t & (G - 1), wk0 = t >> gsh;  // this thread's column and first row in stores
     const int K = TS * L;  // positions of each instance per tile
     const int S = K * G;   // = T L outputs per tile
     const int my0 = lt * L;
@@ -92,12 +95,13 @@ __global__ void __launch_bounds__(512)
                     st_c[sidx(row0 + j)] = c[j];
             }
             __syncthreads();
-            const int cols = (int)V.count;
-            for (int i = t; i < tile_n * G; i += T) {
-                const int col = i & (G - 1), k = i >> gsh;  // written k-major
-                if (col < cols) {
-                    const u64 e = o0 + (base + (u64)k) * stride + (u64)col;
-                    const int slot = sidx(col * K + k);
+            // Written k-major: T is a multiple of G, so thread t always writes
+            // column t mod G, at positions t / G, t / G + TS, ...
+            if (wcol < (int)V.count) {
+                u64 e = o0 + (base + (u64)wk0) * stride + (u64)wcol;
+                const u64 step = (u64)TS * stride;
+                for (int k = wk0; k < tile_n; k += TS, e += step) {
+                    const int slot = sidx(wcol * K + k);
                     if (out_r)
                         out_r[e] = __longlong_as_double((long long)st_r[slot]);
                     if (out_c)
@@ -125,28 +129,51 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// The tuned tile of the vector kernel: 8 numbers per thread in blocks of
+// 128 threads on the CRT route. Unlike the instance-major kernel, every
+// thread holds its own instance's parameters, and 16 numbers per thread no
+// longer fit the register budget of five resident blocks per SM (the
+// compiler spills); 8 do, and five blocks of 8 outrun four of 16.
+constexpr int kVecTunedThreads = 128;
+constexpr int kVecTunedL = 8;
+
+template <int L, int MODEXP>
+constexpr bool vec_tuned()
+{
+    return L == kVecTunedL && MODEXP == MODEXP_CRT32;
+}
+
+template <int L, int MODEXP, int DIV>
+auto vec_kernel(int threads)
+{
+    if constexpr (vec_tuned<L, MODEXP>())
+        if (threads == kVecTunedThreads)
+            return k_generate_vec<L, MODEXP, DIV, kVecTunedThreads>;
+    return k_generate_vec<L, MODEXP, DIV, 0>;
+}
+
 // Every division route gives the same bits, so the vector kernel is
 // instantiated for the integer and reciprocal routes (the others map to the
 // reciprocal one) and for the exact-rational reading.
 template <int DIV>
-const void *vec_kernel_ptr_d(int L, int modexp)
+const void *vec_kernel_ptr_d(int L, int modexp, int threads)
 {
     if (modexp == MODEXP_CRT32) {
         if (L == 16)
-            return (const void *)k_generate_vec<16, MODEXP_CRT32, DIV>;
+            return (const void *)vec_kernel<16, MODEXP_CRT32, DIV>(threads);
         if (L == 8)
-            return (const void *)k_generate_vec<8, MODEXP_CRT32, DIV>;
+            return (const void *)vec_kernel<8, MODEXP_CRT32, DIV>(threads);
         if (L == 4)
-            return (const void *)k_generate_vec<4, MODEXP_CRT32, DIV>;
+            return (const void *)vec_kernel<4, MODEXP_CRT32, DIV>(threads);
         if (L == 2)
-            return (const void *)k_generate_vec<2, MODEXP_CRT32, DIV>;
+            return (const void *)vec_kernel<2, MODEXP_CRT32, DIV>(threads);
     } else {
         if (L == 8)
-            return (const void *)k_generate_vec<8, MODEXP_MONT64, DIV>;
+            return (const void *)vec_kernel<8, MODEXP_MONT64, DIV>(threads);
         if (L == 4)
-            return (const void *)k_generate_vec<4, MODEXP_MONT64, DIV>;
+            return (const void *)vec_kernel<4, MODEXP_MONT64, DIV>(threads);
         if (L == 2)
-            return (const void *)k_generate_vec<2, MODEXP_MONT64, DIV>;
+            return (const void *)vec_kernel<2, MODEXP_MONT64, DIV>(threads);
     }
     return nullptr;
 }
@@ -159,9 +186,9 @@ int vec_div(int divide)
 const void *vec_kernel_ptr(const GenLaunch &g)
 {
     switch (vec_div(g.divide)) {
-    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp);
-    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp);
-    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp);
+    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp, g.threads);
+    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp, g.threads);
+    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp, g.threads);
     }
 }
 
@@ -171,7 +198,7 @@ cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
                          uint64_t *out_c, int TS, cudaStream_t stream)
 {
     const size_t smem = vec_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = k_generate_vec<L, MODEXP, DIV>;
+    auto kern = vec_kernel<L, MODEXP, DIV>(g.threads);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -205,6 +232,12 @@ cudaError_t launch_vec_d(const GenLaunch &g, const DeviceTables &t, const WorkIt
 }
 
 }  // namespace
+
+int vec_numbers_per_thread(int L, int modexp, int threads)
+{
+    return modexp == MODEXP_CRT32 && threads == kVecTunedThreads && L > kVecTunedL ? kVecTunedL
+                                                                                     : L;
+}
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
 {
