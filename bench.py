@@ -40,6 +40,7 @@ import workload  # noqa: E402
 METRIC = "Gnumbers/s float64 on 1 GB300, % int-pipe/HBM roofline; served p50/p99 latency"
 UNIT = "Gnumbers/s"
 WORKLOAD = "bulk_1024x2^20"
+FORMS = ("plain", "batched", "served", "fused", "interleaved")
 
 
 def parse_args(argv=None):
@@ -52,6 +53,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the plain / batched / served forms")
+    ap.add_argument("--forms", default=",".join(FORMS),
+                    help="comma-separated subset of the forms to run (profiling runs)")
+    ap.add_argument("--parents", type=int, default=1024,
+                    help="split parents of the interleaved form (small profiling runs only)")
     ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
     ap.add_argument("--instances", type=int, default=0,
                     help="override the instance count (small profiling runs only)")
@@ -359,12 +364,13 @@ def form_batched(R, torch, device, peak_alu, rank) -> dict:
     return res
 
 
-def form_fused(R, torch, device, peak_alu, rank) -> dict:
+def form_fused(R, torch, device, peak_alu, rank, k=0, n=0) -> dict:
     """Fused consumer: the bulk workload (1024 x 2^20, e uniform in [3, 65537]) binned into
     the frequency-test histogram (D = 1, 2^20 bins) and the serial-test histogram (D = 2,
-    1024^2 bins) inside the generation kernel; nothing is written per output."""
+    1024^2 bins) inside the generation kernel; nothing is written per output. k and n
+    override the instance count and stream length (small profiling runs)."""
     cfg = workload.CONFIGS["bulk_1024x2^20"]
-    k, n = cfg["instances"], cfg["count"]
+    k, n = k or cfg["instances"], n or cfg["count"]
     ctx = R.Context(k, device=device, chunk=n)
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
                               cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
@@ -614,14 +620,21 @@ def run_ours(args) -> int:
                          "api": "rsaprng_generate_batch_host (pinned host output)"}
         del h_out
     if not args.no_forms:
-        # The plain, batched and served forms of the same path on this GPU.
-        result["forms"] = {
-            "plain_1x1e6": form_plain(R, torch, dist.local_rank, peak_alu, dist.rank),
-            "batched_1e5_lognormal": form_batched(R, torch, dist.local_rank, peak_alu, dist.rank),
-            "serving_1e6": form_served(R, torch, dist.local_rank, peak_alu, dist.rank),
-            "fused_histogram_bulk": form_fused(R, torch, dist.local_rank, peak_alu, dist.rank),
-            "split_interleaved": form_interleaved(R, torch, dist.local_rank, peak_alu, dist.rank),
-        }
+        # The plain, batched, served, fused and interleaved forms of the same path on this GPU.
+        want = set(args.forms.split(","))
+        unknown = want - set(FORMS)
+        if unknown:
+            raise SystemExit(f"unknown forms: {sorted(unknown)}")
+        lr, rk = dist.local_rank, dist.rank
+        runs = (("plain_1x1e6", "plain", lambda: form_plain(R, torch, lr, peak_alu, rk)),
+                ("batched_1e5_lognormal", "batched",
+                 lambda: form_batched(R, torch, lr, peak_alu, rk)),
+                ("serving_1e6", "served", lambda: form_served(R, torch, lr, peak_alu, rk)),
+                ("fused_histogram_bulk", "fused",
+                 lambda: form_fused(R, torch, lr, peak_alu, rk, args.instances, args.count)),
+                ("split_interleaved", "interleaved",
+                 lambda: form_interleaved(R, torch, lr, peak_alu, rk, parents=args.parents)))
+        result["forms"] = {name: fn() for name, key, fn in runs if key in want}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)
     if dist.rank == 0:

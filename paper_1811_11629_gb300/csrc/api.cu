@@ -139,15 +139,18 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
     return g;
 }
 
+static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nvecs, bool want_r,
+                            bool want_c);
+
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
                uint64_t tuple, uint64_t stride)
 {
-    // The pieces are sized for the generation kernel's resident blocks, in
-    // tiles of the kernel that runs the plan.
-    const GenLaunch full = ctx_launch(c, cfg, ~0ULL, true, false);
-    const int L = stride > 1 ? vec_numbers_per_thread(full.L, full.modexp, full.threads) : full.L;
-    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)L, (uint64_t)full.grid};
+    // The pieces are sized for the resident blocks and the tiles of the
+    // kernel that runs the plan.
+    const GenLaunch full = stride > 1 ? vec_launch(c, cfg, ~0ULL, true, false)
+                                      : ctx_launch(c, cfg, ~0ULL, true, false);
+    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid};
     return build_plan_core(c->h_params.data(), c->count, cfg.modexp, geo, nreq, ids, counts,
                            offsets, chunk, hp, tuple, stride);
 }
@@ -756,7 +759,7 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
         return fail(RSAPRNG_ERR_ARG, "generate_batch: no output buffer");
     cudaSetDevice(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    HostPlan hp;
+    HostPlan &hp = c->hp_direct;
     int rc = build_plan(c, c->cfg, nreq, ids, counts, out_offsets, c->cfg.chunk, hp);
     if (rc)
         return rc;
@@ -796,7 +799,7 @@ int rsaprng_generate_interleaved(rsaprng_ctx *c, uint64_t ngroups, uint32_t Mv,
     for (uint64_t g = 0; g < ngroups; g++)
         for (uint32_t j = 0; j < Mv; j++)
             offs[g * Mv + j] = g * N * Mv + j;
-    HostPlan hp;
+    HostPlan &hp = c->hp_direct;
     int rc = build_plan(c, c->cfg, k, ids, counts.data(), offs.data(), c->cfg.chunk, hp, 1, Mv);
     if (rc)
         return rc;
@@ -838,7 +841,7 @@ int rsaprng_histogram(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
     // Tuples are counted from each request's start: every request is placed
     // at offset 0, so a piece's offset is its position in its request.
     const std::vector<uint64_t> zero(nreq, 0);
-    HostPlan hp;
+    HostPlan &hp = c->hp_direct;
     int rc = build_plan(c, c->cfg, nreq, ids, counts, zero.data(), c->cfg.chunk, hp, D);
     if (rc)
         return rc;

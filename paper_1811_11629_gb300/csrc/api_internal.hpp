@@ -64,6 +64,7 @@ struct rsaprng_ctx {
     size_t occ_smem[4][4][2][5];
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
+    rsaprng::HostPlan hp_direct;  // host plan of the direct calls, rebuilt in place
 };
 
 namespace rsaprng {

@@ -34,6 +34,70 @@ uint64_t cost_per_number(uint32_t e)
 // before it, so the split is no finer than that.
 constexpr uint64_t kPiecesPerBlock = 1;
 
+// The vector kernel's units (groups of up to G streams side by side) all
+// cost about the same when the streams have one length, so the persistent
+// launch runs them in rounds of `grid` blocks and a last round that is only
+// partly full idles the rest. Two ways to more units: cutting every stream
+// into P pieces (the skip-sum pre-pass then visits (P - 1) / P of the
+// outputs once more), and narrower groups (G / 2 streams of TS * 2 threads:
+// one more shuffle level in the segmented scan, rows of half the width).
+// P stays within a few rounds' worth (kVecRounds).
+constexpr uint64_t kVecRounds = 4;
+// The skip-sum pass over one output, in the units of cost_per_number: one
+// 32-bit-multiplier skip step and one add, measured at 17 % of a whole
+// output at e = 3 (cost 10) on GB300.
+constexpr double kPrepCostPerNumber = 1.7;
+// Score lost per halving of G (the extra scan level, narrower rows).
+constexpr double kVecNarrowCost = 0.01;
+// Pieces shorter than this many tiles are not worth their start-up.
+constexpr uint64_t kVecMinTiles = 8;
+
+// Units the vector kernel would get from the requests uncut: runs of up to G
+// requests (in instance order) of one length whose first outputs are
+// neighbours.
+static uint64_t vector_units(const std::vector<uint64_t> &order, const uint32_t *ids,
+                             const uint64_t *counts, const uint64_t *offsets, uint64_t G)
+{
+    uint64_t units = 0, run = 0, prev = 0;
+    for (uint64_t r : order) {
+        if (counts[r] == 0)
+            continue;
+        const bool join = run > 0 && run < G && counts[r] == counts[prev] &&
+                          offsets[r] == offsets[prev] + 1 && ids[r] != ids[prev];
+        run = join ? run + 1 : 1;
+        units += join ? 0 : 1;
+        prev = r;
+    }
+    return units;
+}
+
+double vec_plan_score(uint64_t units, uint64_t grid, uint64_t p, double prep_share)
+{
+    if (units == 0 || grid == 0 || p == 0)
+        return 0.0;
+    const uint64_t u = units * p;
+    const uint64_t rounds = (u + grid - 1) / grid;
+    const double fill = (double)u / (double)(rounds * grid);
+    return fill / (1.0 + prep_share * (double)(p - 1) / (double)p);
+}
+
+uint64_t vec_pieces_per_stream(uint64_t units, uint64_t grid, uint64_t max_pieces,
+                               double prep_share)
+{
+    if (units == 0 || grid == 0)
+        return 1;
+    const uint64_t pmax = std::max<uint64_t>(
+        1, std::min(max_pieces, kVecRounds * ((grid + units - 1) / units)));
+    double best = 0.0;
+    for (uint64_t p = 1; p <= pmax; p++)
+        best = std::max(best, vec_plan_score(units, grid, p, prep_share));
+    // the smallest P within 3 % of the best: fewer pieces, less planning
+    for (uint64_t p = 1; p <= pmax; p++)
+        if (vec_plan_score(units, grid, p, prep_share) >= 0.97 * best)
+            return p;
+    return 1;
+}
+
 int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const PlanGeometry &geo,
                     uint64_t nreq, const uint32_t *ids, const uint64_t *counts,
                     const uint64_t *offsets, uint64_t chunk, HostPlan &hp, uint64_t tuple,
@@ -49,7 +113,8 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     if (chunk == 0)
         chunk = ~0ULL;
     // Group requests by instance, keeping array order inside each instance.
-    std::vector<uint64_t> order(nreq);
+    std::vector<uint64_t> &order = hp.tmp.order;
+    order.resize(nreq);
     uint64_t work = 0;
     for (uint64_t i = 0; i < nreq; i++) {
         if (ids[i] >= ninst)
@@ -66,26 +131,55 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     // Cost of one piece: the work spread over the resident blocks of the
     // launch, kPiecesPerBlock pieces each; pieces are whole tiles.
     uint64_t tile = geo.threads * geo.L * std::max<uint64_t>(1, tuple);
-    // The vector kernel puts G instances in a block, each with TS L positions
-    // per tile: pieces are whole tiles of it, and there are G times as many
-    // pieces to spread over the resident blocks.
-    uint64_t per_block = 1;
-    if (stride > 1) {
-        hp.vec_ts = vec_threads_per_instance((int)geo.threads, stride);
-        per_block = geo.threads / (uint64_t)hp.vec_ts;
-        tile = (uint64_t)hp.vec_ts * geo.L;
-    }
-    const uint64_t piece_cost =
-        std::max<uint64_t>(1, work / (geo.grid * kPiecesPerBlock * per_block));
-    if (tuple > 1 && chunk != ~0ULL)
-        chunk = std::max(tile, chunk / tile * tile);
     std::stable_sort(order.begin(), order.end(),
                      [&](uint64_t x, uint64_t y) { return ids[x] < ids[y]; });
+    // The vector kernel puts G instances in a block, each with TS = T / G
+    // threads and TS L positions per tile; pieces are whole tiles of it.
+    // Every stream is cut into the same number of pieces; G and the pieces
+    // per stream are chosen together for the rounds of vector units.
+    uint64_t vec_pieces = 0;
+    if (stride > 1) {
+        const uint64_t G0 = geo.threads / (uint64_t)vec_threads_per_instance((int)geo.threads, stride);
+        const uint64_t Gmin = std::max<uint64_t>(geo.threads / 32, std::max<uint64_t>(1, G0 / 4));
+        uint64_t longest = 0, numbers = 0;
+        for (uint64_t i = 0; i < nreq; i++) {
+            longest = std::max(longest, counts[i]);
+            numbers += counts[i];
+        }
+        const double prep_share =
+            numbers ? kPrepCostPerNumber * (double)numbers / (double)std::max<uint64_t>(1, work)
+                    : 0.0;
+        uint64_t bestG = G0;
+        vec_pieces = 1;
+        double best = -1.0, narrow = 1.0;
+        for (uint64_t G = G0; G >= Gmin; G /= 2, narrow -= kVecNarrowCost) {
+            const uint64_t units = vector_units(order, ids, counts, offsets, G);
+            const uint64_t tileG = (geo.threads / G) * geo.L;
+            const uint64_t p =
+                vec_pieces_per_stream(units, geo.grid, longest / (kVecMinTiles * tileG), prep_share);
+            const double sc = vec_plan_score(units, geo.grid, p, prep_share) * narrow;
+            if (sc > best) {
+                best = sc;
+                bestG = G;
+                vec_pieces = p;
+            }
+            if (G == 1)
+                break;
+        }
+        hp.vec_ts = (int)(geo.threads / bestG);
+        tile = (uint64_t)hp.vec_ts * geo.L;
+    }
+    const uint64_t piece_cost = std::max<uint64_t>(1, work / (geo.grid * kPiecesPerBlock));
+    if (tuple > 1 && chunk != ~0ULL)
+        chunk = std::max(tile, chunk / tile * tile);
     struct Piece {
         uint64_t offset, len, out;
     };
     std::vector<Piece> pieces;
-    std::vector<uint64_t> item_cost, item_pos;
+    // per item: its cost, and its rank among the pieces of its stream
+    std::vector<uint64_t> &item_cost = hp.tmp.cost, &item_rank = hp.tmp.rank;
+    item_cost.clear();
+    item_rank.clear();
     for (uint64_t g0 = 0; g0 < nreq;) {
         uint64_t g1 = g0;
         const uint32_t id = ids[order[g0]];
@@ -96,7 +190,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         uint64_t total = 0;
         for (uint64_t k = g0; k < g1; k++)
             total += counts[order[k]];
-        const uint64_t npieces = (total * w + piece_cost - 1) / piece_cost;
+        const uint64_t npieces = vec_pieces ? vec_pieces : (total * w + piece_cost - 1) / piece_cost;
         uint64_t len = npieces > 1 ? (total + npieces - 1) / npieces : total;
         len = (len + tile - 1) / tile * tile;
         const uint64_t cut = std::max<uint64_t>(1, std::min(chunk, len));
@@ -121,7 +215,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
             WorkItem it{id, WI_FROM_STATE | WI_WRITEBACK, pieces[0].len, pieces[0].out, 0, 0};
             hp.items.push_back(it);
             item_cost.push_back(pieces[0].len * w);
-            item_pos.push_back(0);
+            item_rank.push_back(0);
             continue;
         }
         PrepGroup grp{id, (uint32_t)hp.chunks.size(), (uint32_t)pieces.size(), 0};
@@ -134,31 +228,53 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
             hp.chunks.push_back(pc);
             hp.items.push_back(it);
             item_cost.push_back(pieces[k].len * w);
-            item_pos.push_back(pieces[k].offset);
+            item_rank.push_back(k);
         }
     }
     if (hp.items.size() > 0xFFFFFFF0ULL || hp.chunks.size() > 0xFFFFFFF0ULL)
         return fail(RSAPRNG_ERR_ARG, "plan too large");
     // Longest-processing-time-first order for the persistent launch. In the
     // interleaved order (stride > 1) the outputs of different instances at
-    // the same position share memory sectors: pieces are ordered by position
-    // instead, so those writes happen side by side and merge in L2.
-    const bool ordered =
-        stride > 1 ? std::is_sorted(item_pos.begin(), item_pos.end())
-                   : std::is_sorted(item_cost.begin(), item_cost.end(),
-                                    [](uint64_t x, uint64_t y) { return x > y; });
-    if (!ordered) {
-        std::vector<uint32_t> perm(hp.items.size()), where(hp.items.size());
-        for (size_t i = 0; i < perm.size(); i++)
-            perm[i] = (uint32_t)i;
-        if (stride > 1)
-            std::stable_sort(perm.begin(), perm.end(),
-                             [&](uint32_t x, uint32_t y) { return item_pos[x] < item_pos[y]; });
-        else
+    // the same position share memory sectors: pieces are ordered by their
+    // rank in the stream instead (a stable counting sort; the streams of a
+    // vector have one length and are cut alike, so rank is position), and
+    // those writes happen side by side and merge in L2.
+    const size_t ni = hp.items.size();
+    std::vector<uint32_t> &perm = hp.tmp.perm, &where = hp.tmp.where;
+    bool ordered = true;
+    if (stride > 1) {
+        uint64_t ranks = 0;
+        for (size_t i = 0; i < ni; i++) {
+            ranks = std::max(ranks, item_rank[i] + 1);
+            ordered = ordered && (i == 0 || item_rank[i - 1] <= item_rank[i]);
+        }
+        if (!ordered) {
+            std::vector<uint64_t> &start = hp.tmp.order;  // reused: one slot per rank
+            start.assign(ranks + 1, 0);
+            for (size_t i = 0; i < ni; i++)
+                start[item_rank[i] + 1]++;
+            for (uint64_t r = 0; r < ranks; r++)
+                start[r + 1] += start[r];
+            perm.resize(ni);
+            for (size_t i = 0; i < ni; i++)
+                perm[start[item_rank[i]]++] = (uint32_t)i;
+        }
+    } else {
+        ordered = std::is_sorted(item_cost.begin(), item_cost.end(),
+                                 [](uint64_t x, uint64_t y) { return x > y; });
+        if (!ordered) {
+            perm.resize(ni);
+            for (size_t i = 0; i < ni; i++)
+                perm[i] = (uint32_t)i;
             std::stable_sort(perm.begin(), perm.end(),
                              [&](uint32_t x, uint32_t y) { return item_cost[x] > item_cost[y]; });
-        std::vector<WorkItem> sorted(hp.items.size());
-        for (size_t i = 0; i < perm.size(); i++) {
+        }
+    }
+    if (!ordered) {
+        std::vector<WorkItem> &sorted = hp.tmp.sorted;
+        sorted.resize(ni);
+        where.resize(ni);
+        for (size_t i = 0; i < ni; i++) {
             sorted[i] = hp.items[perm[i]];
             where[perm[i]] = (uint32_t)i;
         }

@@ -18,6 +18,13 @@ struct HostPlan {
     uint64_t stride = 1;  // element distance between consecutive outputs of a request
     std::vector<VecGroup> vecs;  // stride > 1: blocks' units of the vector kernel
     int vec_ts = 0;              // threads per instance in the vector kernel
+    // Working storage of the planner, kept so that a plan rebuilt in the same
+    // HostPlan reuses its capacity.
+    struct Scratch {
+        std::vector<uint64_t> order, cost, rank;
+        std::vector<uint32_t> perm, where;
+        std::vector<WorkItem> sorted;
+    } tmp;
 };
 
 // Shape of the generation launch the pieces are sized for.
@@ -38,6 +45,17 @@ uint64_t cost_per_number(uint32_t e);
 // and a vector of `stride` instances: G = threads / TS instances per block,
 // the smallest power of two >= stride between threads / 32 and threads / 4.
 int vec_threads_per_instance(int threads, uint64_t stride);
+
+// Vector plans: `units` groups of equal cost run on `grid` resident blocks,
+// every stream cut into p pieces. The score is the fill of the last round
+// over the cost of the skip-sum pass on the (p - 1) / p outputs that need
+// it, prep_share being that pass's cost per output relative to generating
+// one.
+double vec_plan_score(uint64_t units, uint64_t grid, uint64_t p, double prep_share);
+// The p in [1, max_pieces] (and at most a few rounds' worth) that scores
+// within 3 % of the best, smallest first.
+uint64_t vec_pieces_per_stream(uint64_t units, uint64_t grid, uint64_t max_pieces,
+                               double prep_share);
 
 // Cuts requests (instance ids[i], counts[i] outputs, written from element
 // offsets[i], consecutive outputs `stride` elements apart) into work items:

@@ -233,16 +233,23 @@ static double plan_time_ms(int k, uint64_t stride)
     }
     const PlanGeometry geo{128, 16, 760};
     HostPlan hp;
-    const auto t0 = std::chrono::steady_clock::now();
-    build_plan_core(P.data(), k, RSAPRNG_MODEXP_CRT32, geo, k, ids.data(), cnt.data(), off.data(),
-                    0, hp, 1, stride);
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    // first into a fresh plan, then again into the same one (the library's
+    // direct calls keep one per context)
+    double ms[2];
+    for (double &t : ms) {
+        const auto t0 = std::chrono::steady_clock::now();
+        build_plan_core(P.data(), k, RSAPRNG_MODEXP_CRT32, geo, k, ids.data(), cnt.data(),
+                        off.data(), 0, hp, 1, stride);
+        t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return std::max(ms[0], ms[1]);
 }
 
 int main(int argc, char **argv)
 {
     if (argc > 1 && std::string(argv[1]) == "--time") {
-        std::printf("plan_ms %.2f %.2f\n", plan_time_ms(32768, 1), plan_time_ms(32768, 32));
+        const double contiguous = plan_time_ms(32768, 1), interleaved = plan_time_ms(32768, 32);
+        std::printf("plan_ms %.2f %.2f\n", contiguous, interleaved);
         return 0;
     }
     const int cases = argc > 1 ? std::atoi(argv[1]) : 3000;
@@ -275,6 +282,40 @@ int main(int argc, char **argv)
         if (rc != RSAPRNG_OK) {
             std::printf("CRT exponents refused on the CRT route (rc=%d)\n", rc);
             failures++;
+        }
+    }
+    // 6. pieces per stream of the vector kernel: never more than allowed, the
+    // last round at least as full as uncut, nearly full where cutting can
+    // make it so, and no cut when the pre-pass costs as much as an output
+    for (double share : {0.0, 0.05, 0.2, 1e9}) {
+        for (uint64_t grid : {1ULL, 7ULL, 152ULL, 608ULL, 760ULL, 1216ULL}) {
+            for (uint64_t units = 1; units < 5000; units += 1 + units / 7) {
+                for (uint64_t maxp : {0ULL, 1ULL, 3ULL, 100ULL, 100000ULL}) {
+                    case_no++;
+                    const uint64_t p = vec_pieces_per_stream(units, grid, maxp, share);
+                    auto fill = [&](uint64_t q) {
+                        const uint64_t u = units * q;
+                        return (double)u / (double)(((u + grid - 1) / grid) * grid);
+                    };
+                    // within kVecRounds (4) rounds' worth of pieces
+                    const uint64_t cap = 4 * ((grid + units - 1) / units);
+                    const bool bad =
+                        p < 1 || p > std::max<uint64_t>(1, std::min<uint64_t>(cap, maxp)) ||
+                        fill(p) + 1e-12 < fill(1) || (units % grid == 0 && p != 1) ||
+                        (share <= 0.2 && maxp >= cap && fill(p) < 0.75) ||
+                        (share > 1e6 && p != 1) ||
+                        vec_plan_score(units, grid, p, share) + 1e-12 <
+                            0.97 * vec_plan_score(units, grid, 1, share);
+                    if (bad) {
+                        std::printf("vec pieces: units %llu grid %llu max %llu share %g -> %llu "
+                                    "(fill %.3f)\n",
+                                    (unsigned long long)units, (unsigned long long)grid,
+                                    (unsigned long long)maxp, share, (unsigned long long)p,
+                                    fill(p));
+                        failures++;
+                    }
+                }
+            }
         }
     }
     std::printf("%d cases, %d failures\n", case_no, failures);
