@@ -19,17 +19,41 @@ namespace dev {
 constexpr u64 Q = 0x7FFFFFFFFFFFFFE7ULL;
 constexpr u64 LOW63 = 0x7FFFFFFFFFFFFFFFULL;
 
-// a s mod Q for a < 2^32 and s < Q: the product is below 2^95.
+// a s mod Q for a < 2^32 and s < Q: the product is below 2^95. With
+// p0 = s_lo a and p1 = s_hi a + hi32(p0) (two widening multiply-adds, p1 <
+// 2^64), a s = p1 2^32 + lo32(p0) = H 2^63 + L with H = p1 >> 31 < 2^33 and
+// L = a s mod 2^63; 2^63 = 25 (mod Q) folds it to y = 25 H + L < 2^63 + 2^38,
+// and y >= Q exactly when bit 63 of y + 25 is set, which then is y - Q.
 __device__ __forceinline__ u64 mulmodQ_small(u64 s, u32 a)
 {
-    const u64 p0 = (u64)(u32)s * a;          // s_lo * a
-    const u64 p1 = (u64)(u32)(s >> 32) * a;  // s_hi * a, below 2^63
-    const u64 lo = p0 + (p1 << 32);
-    const u64 hi = (p1 >> 32) + (lo < p0 ? 1 : 0);
-    // x = hi 2^64 + lo = H 2^63 + L63 with H = 2 hi + lo_63 < 2^33
-    const u64 H = (hi << 1) | (lo >> 63);
-    u64 y = H * 25 + (lo & LOW63);  // < 2^63 + 2^38 < 2Q
-    return y >= Q ? y - Q : y;
+    const u64 p0 = (u64)(u32)s * a;
+    const u64 p1 = (u64)(u32)(s >> 32) * a + (p0 >> 32);
+    const u64 H = p1 >> 31;
+    const u64 L = ((p1 & 0x7FFFFFFFULL) << 32) | (u32)p0;
+    const u64 y = H * 25 + L;
+    const u64 z = y + 25;
+    return (z >> 63) ? (z & LOW63) : y;
+}
+
+// acc += x with the carries out of 64 bits counted in cnt (the sum is
+// acc + cnt 2^64).
+__device__ __forceinline__ void add_carry_count(u64 &acc, u32 &cnt, u64 x)
+{
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(acc), "+r"(cnt) : "l"(x));
+}
+
+// k r mod n for r < n by doubling and adding over the bits of k.
+__device__ __forceinline__ u64 mulmod_small_count(u64 k, u64 r, u64 n)
+{
+    u64 t = 0;
+    for (int b = k ? 63 - __clzll((long long)k) : -1; b >= 0; b--) {
+        t = t + t >= n || t + t < t ? t + t - n : t + t;
+        if ((k >> b) & 1) {
+            const u64 u = t + r;
+            t = (u < t || u >= n) ? u - n : u;
+        }
+    }
+    return t;
 }
 
 // x y mod Q for x, y < Q (general 63-bit multiplier).

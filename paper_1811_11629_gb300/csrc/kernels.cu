@@ -23,7 +23,9 @@
 
 namespace rsaprng {
 
+using dev::add_carry_count;
 using dev::add_cong;
+using dev::mulmod_small_count;
 using dev::addmod;
 using dev::mulmodQ;
 using dev::mulmodQ_small;
@@ -31,6 +33,7 @@ using dev::reduce_u64;
 
 namespace {
 
+using tile::FULL;
 using tile::block_exscan_mod;
 using tile::block_reduce_mod;
 using tile::sidx;
@@ -150,58 +153,76 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
 // Skip sums of chunks: for chunk k with start offset o and length len,
 // chunk_s[k] = s a^o mod Q (the skip before its first output) and
 // chunk_sum[k] = sum_{x=1..len} (s a^(o+x) mod Q) mod n, where s is the
-// instance's current skip. One block per chunk, 256 threads x 8 skips a tile.
-// The last chunk of an instance is listed with len = 0: no later chunk needs
-// its sum.
+// instance's current skip. One warp per chunk: the jump a^o is the product
+// of the table powers a^(2^b) over the set bits b of o, two bits per lane
+// and a butterfly over the lanes; the sum runs in tiles of 32 lanes x 8
+// skips and ends in a warp reduction. The last chunk of an instance is
+// listed with len = 0: no later chunk needs its sum.
 constexpr int kPrepT = 256;
 constexpr int kPrepL = 8;
+constexpr int kPrepWarps = kPrepT / 32;
 __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
                                                      const PrepChunk *__restrict__ chunks,
                                                      uint32_t nchunks, u64 *__restrict__ chunk_sum,
                                                      u64 *__restrict__ chunk_s)
 {
-    __shared__ u64 sh_scan[32];
-    __shared__ u64 sh_s0;
-    const int t = threadIdx.x;
-    for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = gridDim.x * kPrepWarps;
+    for (uint32_t k = blockIdx.x * kPrepWarps + (threadIdx.x >> 5); k < nchunks; k += nw) {
         const PrepChunk C = chunks[k];
         const InstParams P = tab.params[C.inst];
         const u64 n = P.n, r64 = P.r64;
         const u32 a = P.a;
         const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
         const u64 *p2k = tab.pow2k + (size_t)P.root * 64;
-        if (t == 0) {
-            u64 s = tab.state_s[C.inst];
-            for (int b = 0; b < 64; b++)
-                if ((C.offset >> b) & 1)
-                    s = mulmodQ(s, p2k[b]);
-            sh_s0 = s;
-            chunk_s[k] = s;
-        }
-        __syncthreads();
-        const u64 s0 = sh_s0;
-        constexpr int S = kPrepT * kPrepL;
-        u64 s_thr = mulmodQ(s0, plin[t * kPrepL]);
+        // a^o: lane l takes bits 2l and 2l + 1 of o
+        const int b0 = 2 * lane;
+        u64 f = ((C.offset >> b0) & 1) ? p2k[b0] : 1;
+        if ((C.offset >> (b0 + 1)) & 1)
+            f = mulmodQ(f, p2k[b0 + 1]);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1)
+            f = mulmodQ(f, __shfl_xor_sync(FULL, f, d));
+        const u64 s0 = mulmodQ(tab.state_s[C.inst], f);
+        if (lane == 0)
+            chunk_s[k] = s0;
+        constexpr int S = 32 * kPrepL;
+        u64 s_thr = mulmodQ(s0, plin[lane * kPrepL]);
         const u64 aS = plin[S];
+        // the lane's sum is acc + carries 2^64 (2^64 = r64 mod n)
         u64 acc = 0;
-        for (u64 base = 0; base < C.len; base += S) {
-            const u64 left = C.len - base;
-            const int my0 = t * kPrepL;
-            const int tile_n = left < (u64)S ? (int)left : S;
+        u32 carries = 0;
+        const int my0 = lane * kPrepL;
+        u64 base = 0;
+        for (; base + S <= C.len; base += S) {  // whole tiles
+            u64 x = s_thr;
+#pragma unroll
+            for (int j = 0; j < kPrepL; j++) {
+                x = mulmodQ_small(x, a);
+                add_carry_count(acc, carries, x);
+            }
+            s_thr = mulmodQ(s_thr, aS);
+        }
+        if (base < C.len) {  // the ragged tail
+            const int tile_n = (int)(C.len - base);
             const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > kPrepL ? kPrepL : tile_n - my0);
             u64 x = s_thr;
 #pragma unroll
             for (int j = 0; j < kPrepL; j++) {
                 x = mulmodQ_small(x, a);
                 if (j < nvalid)
-                    acc = add_cong(acc, x, r64);
+                    add_carry_count(acc, carries, x);
             }
-            s_thr = mulmodQ(s_thr, aS);
         }
-        const u64 tot = block_reduce_mod(reduce_u64(acc, n), n, sh_scan);
-        if (t == 0)
-            chunk_sum[k] = tot;
-        __syncthreads();
+        u64 tot = reduce_u64(acc, n);
+        u64 ncarry = carries;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            tot = addmod(tot, __shfl_xor_sync(FULL, tot, d), n);
+            ncarry += __shfl_xor_sync(FULL, ncarry, d);
+        }
+        if (lane == 0)
+            chunk_sum[k] = addmod(tot, mulmod_small_count(ncarry, r64, n), n);
     }
 }
 
@@ -234,9 +255,11 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
         u64 m = addmod(m0, block_exscan_mod(run, n, sh_scan, total), n);
         for (uint32_t j = j0; j < j1; j++) {
             const uint32_t k = G.first + j;
-            WorkItem &w = items[chunks[k].item];
-            w.m0 = m;
-            w.s0 = chunk_s[k];
+            const uint32_t it = chunks[k].item;
+            if (it != kNoItem) {
+                items[it].m0 = m;
+                items[it].s0 = chunk_s[k];
+            }
             m = addmod(m, chunk_sum[k], n);
         }
         __syncthreads();  // sh_scan is reused by the next group
@@ -510,7 +533,8 @@ cudaError_t launch_prep_sums(const DeviceTables &t, const PrepChunk *chunks, uin
 {
     if (nchunks == 0)
         return cudaSuccess;
-    const int grid = (int)(nchunks < 65535u ? nchunks : 65535u);
+    const uint32_t blocks = (nchunks + kPrepWarps - 1) / kPrepWarps;
+    const int grid = (int)(blocks < 65535u ? blocks : 65535u);
     k_prep_sums<<<grid, kPrepT, 0, stream>>>(t, chunks, nchunks, chunk_sum, chunk_s);
     return cudaGetLastError();
 }

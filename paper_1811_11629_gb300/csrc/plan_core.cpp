@@ -52,6 +52,15 @@ constexpr double kVecNarrowCost = 0.01;
 // Pieces shorter than this many tiles are not worth their start-up.
 constexpr uint64_t kVecMinTiles = 8;
 
+// The skip-sum pre-pass runs one warp per chunk entry. A piece's range is
+// cut into segments of at most kPrepSegMin outputs, or longer ones when the
+// ranges are long enough to give more than kPrepSegPerBlock segments per
+// resident generation block (several per resident warp of the pre-pass), so
+// that no warp walks a long range alone and the last wave of pre-pass
+// blocks is short.
+constexpr uint64_t kPrepSegMin = 4096;
+constexpr uint64_t kPrepSegPerBlock = 64;
+
 // Units the vector kernel would get from the requests uncut: runs of up to G
 // requests (in instance order) of one length whose first outputs are
 // neighbours.
@@ -281,6 +290,42 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         hp.items.swap(sorted);
         for (auto &pc : hp.chunks)
             pc.item = where[pc.item];
+    }
+    // Skip-sum segments (see kPrepSegMin); the first entry of a piece keeps
+    // its item, the others continue its range.
+    uint64_t prep_total = 0, prep_longest = 0;
+    for (const PrepChunk &pc : hp.chunks) {
+        prep_total += pc.len;
+        prep_longest = std::max(prep_longest, pc.len);
+    }
+    const uint64_t seg = std::max<uint64_t>(
+        kPrepSegMin,
+        (prep_total / std::max<uint64_t>(1, kPrepSegPerBlock * geo.grid) + 255) / 256 * 256);
+    if (prep_longest > seg) {
+        std::vector<PrepChunk> &out = hp.tmp.chunks;
+        out.clear();
+        for (PrepGroup &g : hp.groups) {
+            const uint32_t first = (uint32_t)out.size();
+            for (uint32_t j = g.first; j < g.first + g.count; j++) {
+                PrepChunk c = hp.chunks[j];
+                uint64_t left = c.len;
+                c.len = std::min(left, seg);
+                out.push_back(c);
+                uint64_t off = c.offset + c.len;
+                left -= c.len;
+                while (left > 0) {
+                    const uint64_t l = std::min(left, seg);
+                    out.push_back({c.inst, kNoItem, off, l});
+                    off += l;
+                    left -= l;
+                }
+            }
+            g.first = first;
+            g.count = (uint32_t)(out.size() - first);
+        }
+        if (out.size() > 0xFFFFFFF0ULL)
+            return fail(RSAPRNG_ERR_ARG, "plan too large");
+        hp.chunks.swap(out);
     }
     if (stride > 1) {
         // Units of the vector kernel: up to G items in a row with the same

@@ -24,6 +24,7 @@ struct HostPlan {
         std::vector<uint64_t> order, cost, rank;
         std::vector<uint32_t> perm, where;
         std::vector<WorkItem> sorted;
+        std::vector<PrepChunk> chunks;
     } tmp;
 };
 

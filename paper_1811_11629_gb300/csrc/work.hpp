@@ -31,6 +31,10 @@ struct PrepChunk {
     uint64_t offset;
     uint64_t len;
 };
+// A chunk entry with item = kNoItem continues the skip-sum range of the
+// entry before it (long ranges are cut into segments so that the pre-pass
+// spreads over many warps); it starts no work item.
+constexpr uint32_t kNoItem = 0xFFFFFFFFu;
 // A run of consecutive PrepChunk entries (in stream order) of one instance.
 struct PrepGroup {
     uint32_t inst;

@@ -137,14 +137,22 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
     std::vector<int64_t> item_off(hp.items.size(), -1);
     for (const auto &g : hp.groups) {
         uint64_t expect = 0;
-        for (uint32_t j = 0; j < g.count; j++) {
+        for (uint32_t j = 0; j < g.count;) {
             const PrepChunk &c = hp.chunks[g.first + j];
             CHECK(c.inst == g.inst && c.item < hp.items.size(), "chunk of another instance");
             const WorkItem &w = hp.items[c.item];
             CHECK(w.inst == g.inst, "chunk item of another instance");
             CHECK(c.offset == expect, "chunk offsets not contiguous");
-            const bool last = j + 1 == g.count;
-            CHECK(c.len == (last ? 0 : w.count), "chunk length");
+            // segments without an item continue the piece's skip-sum range
+            uint64_t covered = c.len;
+            for (j++; j < g.count && hp.chunks[g.first + j].item == kNoItem; j++) {
+                const PrepChunk &sg = hp.chunks[g.first + j];
+                CHECK(sg.inst == g.inst && sg.len > 0 && sg.offset == expect + covered,
+                      "skip-sum segment out of place");
+                covered += sg.len;
+            }
+            const bool last = j == g.count;
+            CHECK(covered == (last ? 0 : w.count), "chunk length");
             CHECK(!(w.flags & WI_FROM_STATE), "piece after the first reads the state");
             CHECK(((w.flags & WI_WRITEBACK) != 0) == last, "write-back not on the last piece");
             item_off[c.item] = (int64_t)c.offset;

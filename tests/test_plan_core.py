@@ -40,6 +40,10 @@ MUTANTS = {
     "last_chunk_summed": ("last ? 0 : pieces[k].len", "pieces[k].len"),
     "shortest_first": ("return item_cost[x] > item_cost[y];", "return item_cost[x] < item_cost[y];"),
     "groups_of_strangers": ("&&\n                   hp.items[j].out_off == hp.items[j - 1].out_off + 1)", ")"),
+    "segment_drops_tail": ("                    off += l;\n                    left -= l;",
+                           "                    left -= l;"),
+    "segment_keeps_item": ("out.push_back({c.inst, kNoItem, off, l});",
+                           "out.push_back({c.inst, c.item, off, l});"),
 }
 
 
