@@ -40,7 +40,7 @@ import workload  # noqa: E402
 METRIC = "Gnumbers/s float64 on 1 GB300, % int-pipe/HBM roofline; served p50/p99 latency"
 UNIT = "Gnumbers/s"
 WORKLOAD = "bulk_1024x2^20"
-FORMS = ("plain", "batched", "served", "fused", "interleaved")
+FORMS = ("plain", "batched", "served", "fused", "interleaved", "split_full")
 
 
 def parse_args(argv=None):
@@ -441,6 +441,48 @@ def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> d
     return out
 
 
+def form_split_full(R, torch, device, peak_alu, rank, slice_parents: int = 1024) -> dict:
+    """The whole split workload: 65536 parents x 32 substreams x 2^16 (2^37 outputs, u64 +
+    f64 = 2 TiB, more than HBM holds), generated in slices of slice_parents parents into one
+    reused output buffer; throughput over all slices, substream-major and interleaved."""
+    cfg = workload.CONFIGS["split_65536x32x2^16"]
+    parents, mv, n = cfg["instances"], cfg["substreams"], cfg["count"]
+    ctx = R.Context(parents * (mv + 1), device=device)
+    first = ctx.create_seeded(workload.instance_seeds(cfg["master"], parents, first=rank * parents),
+                              cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    kids = np.stack([ctx.split(first + i, mv) for i in range(parents)]).astype(np.uint32)
+    per = slice_parents * mv * n
+    oc = torch.empty(per, dtype=torch.int64, device="cuda")
+    orr = torch.empty(per, dtype=torch.float64, device="cuda")
+    counts = np.full(slice_parents * mv, n, np.uint64)
+
+    def substream_major(s):
+        ctx.generate_batch(kids[s:s + slice_parents].reshape(-1), counts, out_r=orr, out_c=oc)
+
+    def interleaved(s):
+        ctx.generate_interleaved(kids[s:s + slice_parents], n, out_r=orr, out_c=oc)
+
+    out = {}
+    for name, fn in (("substream_major", substream_major), ("interleaved", interleaved)):
+        fn(0)  # warm-up slice (continues the first slice's streams; the timed pass covers all)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for s in range(0, parents, slice_parents):
+            fn(s)
+        b.record()
+        torch.cuda.synchronize()
+        dt = a.elapsed_time(b) / 1e3
+        out[name] = {"value": round(parents * mv * n / dt / 1e9, 3), "unit": UNIT,
+                     "s": round(dt, 3), "hbm_GBps": round(16 * parents * mv * n / dt / 1e9, 1)}
+    out["shape"] = (f"{parents} parents x {mv} substreams x {n} = 2^37 outputs, u64 + f64, "
+                    f"{parents // slice_parents} slices of {slice_parents} parents into one "
+                    f"{16 * per // 2**30} GiB buffer")
+    ctx.close()
+    del oc, orr
+    torch.cuda.empty_cache()
+    return out
+
+
 def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
     [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
@@ -633,7 +675,9 @@ def run_ours(args) -> int:
                 ("fused_histogram_bulk", "fused",
                  lambda: form_fused(R, torch, lr, peak_alu, rk, args.instances, args.count)),
                 ("split_interleaved", "interleaved",
-                 lambda: form_interleaved(R, torch, lr, peak_alu, rk, parents=args.parents)))
+                 lambda: form_interleaved(R, torch, lr, peak_alu, rk, parents=args.parents)),
+                ("split_full_65536x32x2^16", "split_full",
+                 lambda: form_split_full(R, torch, lr, peak_alu, rk)))
         result["forms"] = {name: fn() for name, key, fn in runs if key in want}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)
