@@ -149,7 +149,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     uint64_t vec_pieces = 0;
     if (stride > 1) {
         const uint64_t G0 = geo.threads / (uint64_t)vec_threads_per_instance((int)geo.threads, stride);
-        const uint64_t Gmin = std::max<uint64_t>(geo.threads / 32, std::max<uint64_t>(1, G0 / 4));
+        const uint64_t Gmin = std::max<uint64_t>(1, geo.threads / 32);
         uint64_t longest = 0, numbers = 0;
         for (uint64_t i = 0; i < nreq; i++) {
             longest = std::max(longest, counts[i]);
@@ -290,6 +290,16 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         hp.items.swap(sorted);
         for (auto &pc : hp.chunks)
             pc.item = where[pc.item];
+        if (stride > 1) {  // the vector units below read rank and cost in the new order
+            std::vector<uint64_t> &tmp = hp.tmp.order;
+            tmp.resize(ni);
+            for (size_t i = 0; i < ni; i++)
+                tmp[i] = item_rank[perm[i]];
+            item_rank.swap(tmp);
+            for (size_t i = 0; i < ni; i++)
+                tmp[i] = item_cost[perm[i]];
+            item_cost.swap(tmp);
+        }
     }
     // Skip-sum segments (see kPrepSegMin); the first entry of a piece keeps
     // its item, the others continue its range.
@@ -332,13 +342,35 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         // length whose outputs are neighbours (consecutive instances of a
         // vector at the same positions).
         const uint32_t G = (uint32_t)(geo.threads / (uint64_t)hp.vec_ts);
+        std::vector<uint64_t> &unit_cost = hp.tmp.order;
+        unit_cost.clear();
         for (uint32_t i = 0; i < (uint32_t)hp.items.size();) {
             uint32_t j = i + 1;
+            uint64_t c = item_cost[i];
             while (j < hp.items.size() && j - i < G && hp.items[j].count == hp.items[i].count &&
                    hp.items[j].out_off == hp.items[j - 1].out_off + 1)
-                j++;
+                c = std::max(c, item_cost[j++]);
             hp.vecs.push_back({i, j - i});
+            unit_cost.push_back(c);
             i = j;
+        }
+        // Within a rank (one position range), costliest units first, so that the
+        // launch ends on its cheapest units; units of one vector share their
+        // exponents and cost, and stay side by side.
+        std::vector<uint32_t> &uperm = hp.tmp.perm;
+        uperm.resize(hp.vecs.size());
+        for (uint32_t u = 0; u < (uint32_t)uperm.size(); u++)
+            uperm[u] = u;
+        auto unit_before = [&](uint32_t x, uint32_t y) {
+            const uint64_t rx = item_rank[hp.vecs[x].first], ry = item_rank[hp.vecs[y].first];
+            return rx != ry ? rx < ry : unit_cost[x] > unit_cost[y];
+        };
+        if (!std::is_sorted(uperm.begin(), uperm.end(), unit_before)) {
+            std::stable_sort(uperm.begin(), uperm.end(), unit_before);
+            std::vector<VecGroup> sorted_vecs(uperm.size());
+            for (size_t u = 0; u < uperm.size(); u++)
+                sorted_vecs[u] = hp.vecs[uperm[u]];
+            hp.vecs.swap(sorted_vecs);
         }
     }
     return RSAPRNG_OK;

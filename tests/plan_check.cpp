@@ -211,16 +211,34 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
         const uint32_t G = (uint32_t)(geo.threads / (uint64_t)hp.vec_ts);
         CHECK(hp.vec_ts >= 1 && geo.threads % hp.vec_ts == 0 && hp.vec_ts <= 32 && hp.vec_ts >= 4,
               "threads per instance %d", hp.vec_ts);
-        uint32_t next = 0;
+        // the groups are runs of neighbouring items that together cover every
+        // item once; they run by position, costliest first at one position
+        std::vector<int> seen(hp.items.size(), 0);
+        uint64_t covered = 0, prev_pos = 0, prev_cost = ~0ULL;
         for (const auto &g : hp.vecs) {
-            CHECK(g.first == next && g.count >= 1 && g.count <= G, "group layout");
-            for (uint32_t j = 1; j < g.count; j++) {
-                const WorkItem &a = hp.items[g.first + j - 1], &b = hp.items[g.first + j];
-                CHECK(b.count == a.count && b.out_off == a.out_off + 1, "group members not neighbours");
+            CHECK(g.count >= 1 && g.count <= G && (uint64_t)g.first + g.count <= hp.items.size(),
+                  "group layout");
+            uint64_t cost = 0;
+            for (uint32_t j = 0; j < g.count; j++) {
+                CHECK(!seen[g.first + j]++, "item in two groups");
+                const WorkItem &b = hp.items[g.first + j];
+                cost = std::max(cost, b.count * cost_per_number(std::max(params[b.inst].e,
+                                                                         params[b.inst].eq)));
+                if (j) {
+                    const WorkItem &a = hp.items[g.first + j - 1];
+                    CHECK(b.count == a.count && b.out_off == a.out_off + 1,
+                          "group members not neighbours");
+                }
             }
-            next += g.count;
+            const uint64_t pos = item_off[g.first] < 0 ? 0 : (uint64_t)item_off[g.first];
+            CHECK(pos >= prev_pos, "vector groups not by position");
+            CHECK(pos > prev_pos || cost <= prev_cost, "not costliest first at one position");
+            prev_pos = pos;
+            prev_cost = cost;
+            covered += g.count;
         }
-        CHECK(next == hp.items.size(), "groups cover %u of %zu items", next, hp.items.size());
+        CHECK(covered == hp.items.size(), "groups cover %llu of %zu items",
+              (unsigned long long)covered, hp.items.size());
     } else {
         CHECK(hp.vecs.empty(), "vector groups in a contiguous plan");
     }

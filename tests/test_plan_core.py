@@ -44,6 +44,8 @@ MUTANTS = {
                            "                    left -= l;"),
     "segment_keeps_item": ("out.push_back({c.inst, kNoItem, off, l});",
                            "out.push_back({c.inst, c.item, off, l});"),
+    "units_cheapest_first": ("return rx != ry ? rx < ry : unit_cost[x] > unit_cost[y];",
+                             "return rx != ry ? rx < ry : unit_cost[x] < unit_cost[y];"),
 }
 
 
