@@ -279,6 +279,13 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
     cudaError_t e;
+    // The persistent launch's ticket is reset before the pre-pass, so that the
+    // three kernels follow one another directly (each a programmatic dependent
+    // of the one before).
+    if (dp.nitems && !fresh) {
+        if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
+            return cuda_fail(e, "ticket reset");
+    }
     if (dp.nchunks) {
         if ((e = launch_prep_sums(t, dp.chunks, dp.nchunks, dp.chunk_sum, dp.chunk_s, stream)) !=
             cudaSuccess)
@@ -295,11 +302,8 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
                             : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr,
                                          &dp.occupancy);
         g.stride = dp.stride;
+        g.pdl = dp.nchunks > 0;
         dp.last = g;
-        if (g.persistent && !fresh) {
-            if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
-                return cuda_fail(e, "ticket reset");
-        }
         if (hist)
             e = launch_histogram(g, t, dp.items, dp.nitems, dp.ticket, *hist, stream);
         else if (vec)

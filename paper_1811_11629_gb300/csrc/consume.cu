@@ -68,6 +68,7 @@ template <int L, int MODEXP, int DIV>
 __global__ void __launch_bounds__(512) k_histogram(DeviceTables tab, const WorkItem *__restrict__ items,
                                                    uint32_t nitems, uint32_t *ticket, HistArgs h)
 {
+    tile::pdl_wait();  // the start states of the pieces, from the start-state scan
     extern __shared__ uint32_t dig[];  // S digits of the tile, then the carry (D - 1 <= 7)
     __shared__ u64 sh_scan[32];
     __shared__ uint32_t sh_item;
@@ -175,9 +176,8 @@ cudaError_t launch_hist_t(const GenLaunch &g, const DeviceTables &t, const WorkI
                           uint32_t nitems, uint32_t *ticket, const HistArgs &h, cudaStream_t stream)
 {
     const size_t smem = hist_smem_bytes(g.threads, L);
-    k_histogram<L, MODEXP, DIV><<<g.grid, g.threads, smem, stream>>>(
-        t, items, nitems, g.persistent ? ticket : nullptr, h);
-    return cudaGetLastError();
+    return launch_kernel(k_histogram<L, MODEXP, DIV>, g.grid, g.threads, smem, stream, g.pdl, t,
+                         items, nitems, g.persistent ? ticket : nullptr, h);
 }
 
 // The float digits need r itself, which every division route gives bit for

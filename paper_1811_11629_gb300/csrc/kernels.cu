@@ -34,6 +34,8 @@ using dev::reduce_u64;
 namespace {
 
 using tile::FULL;
+using tile::pdl_trigger;
+using tile::pdl_wait;
 using tile::block_exscan_mod;
 using tile::block_reduce_mod;
 using tile::sidx;
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
                                                   double *__restrict__ out_r,
                                                   u64 *__restrict__ out_c, u64 stride)
 {
+    pdl_wait();  // the start states of the pieces, from the start-state scan
     extern __shared__ u64 smem[];
     __shared__ u64 sh_scan[32];
     __shared__ uint32_t sh_item;
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kPrepT) k_prep_sums(DeviceTables tab,
                                                      uint32_t nchunks, u64 *__restrict__ chunk_sum,
                                                      u64 *__restrict__ chunk_s)
 {
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const uint32_t nw = gridDim.x * kPrepWarps;
     for (uint32_t k = blockIdx.x * kPrepWarps + (threadIdx.x >> 5); k < nchunks; k += nw) {
@@ -239,6 +243,8 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
                                                       const u64 *__restrict__ chunk_s,
                                                       WorkItem *__restrict__ items)
 {
+    pdl_wait();  // the chunk sums of the pre-pass
+    pdl_trigger();
     __shared__ u64 sh_scan[32];
     const int t = threadIdx.x;
     for (uint32_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
@@ -288,9 +294,8 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
         if (e != cudaSuccess)
             return e;
     }
-    kern<<<g.grid, g.threads, smem, stream>>>(t, items, nitems, g.persistent ? ticket : nullptr,
-                                              out_r, out_c, g.stride);
-    return cudaGetLastError();
+    return launch_kernel(kern, g.grid, g.threads, smem, stream, g.pdl, t, items, nitems,
+                         g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride);
 }
 
 template <int L, int MODEXP, int DIV>
@@ -546,9 +551,9 @@ cudaError_t launch_prep_scan(const DeviceTables &t, const PrepGroup *groups, uin
     if (ngroups == 0)
         return cudaSuccess;
     const int grid = (int)(ngroups < 65535u ? ngroups : 65535u);
-    k_prep_scan<<<grid, kScanT, 0, stream>>>(t, groups, ngroups, chunks, chunk_sum, chunk_s,
-                                             items);
-    return cudaGetLastError();
+    // always right after the pre-pass: a programmatic dependent of it
+    return launch_kernel(k_prep_scan, grid, kScanT, 0, stream, true, t, groups, ngroups, chunks,
+                         chunk_sum, chunk_s, items);
 }
 
 cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const uint64_t *c,

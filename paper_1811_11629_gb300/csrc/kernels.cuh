@@ -41,7 +41,28 @@ struct GenLaunch {
     int grid;        // blocks
     bool persistent; // items pulled from *ticket
     uint64_t stride; // element distance between consecutive outputs of a work item
+    bool pdl = false;  // launch as a programmatic dependent of the start-state scan
 };
+
+// Launches kern; with pdl as a programmatic dependent of the kernel before it
+// on the stream (kern must wait in griddepcontrol.wait before it reads what
+// that kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t stream, bool pdl, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // Shared memory bytes the generation kernel needs for a tile.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);

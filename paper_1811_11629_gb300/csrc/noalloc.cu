@@ -142,7 +142,8 @@ int rsaprng_generate_f64_noalloc(rsaprng_ctx *c, rsaprng_id id, uint64_t N, doub
             return RSAPRNG_ERR_CUDA;
         nl += 2;
     }
-    const GenLaunch g = ctx_launch(c, c->cfg, nchunks, true, false);
+    GenLaunch g = ctx_launch(c, c->cfg, nchunks, true, false);
+    g.pdl = nchunks > 1;  // right after the start-state scan
     if ((e = launch_generate(g, t, S->items, nchunks, &S->ticket, d_r, nullptr, st)) !=
         cudaSuccess)
         return RSAPRNG_ERR_CUDA;

@@ -18,6 +18,24 @@ using dev::reduce_u64;
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+// Programmatic dependent launch: a kernel launched as a programmatic
+// dependent may start while the kernel before it on the stream finishes;
+// it waits here, before it reads anything that kernel wrote, until that
+// kernel has completed and its writes are visible (a no-op for a kernel
+// launched the ordinary way).
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Lets the dependent kernel launch once every block of this kernel has
+// started; called at block entry, so the dependent's waiting blocks never
+// hold the place of a block of this kernel that has still to run.
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // Padded shared-memory index: one 8-byte slot of padding every 16 elements
 // spreads the stride-L writes of a warp over the banks.
 __device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
                    const VecGroup *__restrict__ vecs, uint32_t nvecs, uint32_t *ticket,
                    double *__restrict__ out_r, u64 *__restrict__ out_c, u64 stride, int TS)
 {
+    tile::pdl_wait();  // the start states of the pieces, from the start-state scan
     extern __shared__ u64 smem[];
     __shared__ uint32_t sh_item;
     const int T = TB ? TB : (int)blockDim.x, t = threadIdx.x;
@@ -205,10 +206,8 @@ cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
         if (e != cudaSuccess)
             return e;
     }
-    kern<<<g.grid, g.threads, smem, stream>>>(t, items, vecs, nvecs,
-                                              g.persistent ? ticket : nullptr, out_r, out_c,
-                                              g.stride, TS);
-    return cudaGetLastError();
+    return launch_kernel(kern, g.grid, g.threads, smem, stream, g.pdl, t, items, vecs, nvecs,
+                         g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride, TS);
 }
 
 template <int DIV>
