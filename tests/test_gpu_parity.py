@@ -312,6 +312,33 @@ def test_plan_graph_replay(O):
     plan.close()
 
 
+def test_plan_graph_replay_persistent_chunked(O):
+    """Replays of a plan whose pieces outnumber the resident blocks (the persistent launch and
+    its ticket) and whose streams are cut into many chunks (pre-pass, start-state scan and
+    generation launched as programmatic dependents): every replay continues every stream."""
+    ctx = R.Context(64, chunk=2048)
+    ids, par = seeded(ctx, O, master=22, k=40, rule=R.E_UNIFORM, lo=3, hi=257)
+    counts = workload.lognormal_lengths(22, 40, median=150000.0, sigma=0.5, lo=2049, hi=400000)
+    total = int(counts.sum())
+    plan = ctx.plan(ids, counts)
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    plan.capture(out_r=out, stream=s)
+    assert plan.shape()["persistent"] == 1
+    states = [(pr[3], 1) for pr in par]
+    for rep in range(3):
+        plan.replay(stream=s)
+        s.synchronize()
+        g = out.cpu().numpy()
+        off = 0
+        for i in range(len(ids)):
+            n = int(counts[i])
+            states[i] = check_stream(O, par[i], *states[i], None, g[off:off + n])
+            off += n
+    assert plan.info()["chunks"] > 2000
+    plan.close()
+
+
 def test_autotune_bit_identical_and_state_preserved(O):
     ctx = R.Context(64)
     ids, par = seeded(ctx, O, master=21, k=24, rule=R.E_UNIFORM, lo=3, hi=65537)
