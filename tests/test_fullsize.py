@@ -1,5 +1,5 @@
-"""Full-size parity for the stream-splitting, batched and serving workloads, checked
-on sampled outputs (the oracle computes them one by one) and end states."""
+"""Full-size parity for the stream-splitting (substream-major and interleaved), batched and
+serving workloads, checked on sampled outputs (the oracle computes them one by one) and end states."""
 import numpy as np
 import pytest
 
@@ -92,6 +92,65 @@ def test_split_full_size_sampled(O):
             assert np.array_equal(bits(out_r[t].cpu().numpy()), bits(wr))
             for g in range(MV):
                 assert ctx.get_state(int(kids[(i - s0) * MV + g])) == (int(m[g]), int(s[g]))
+
+
+def test_split_interleaved_full_size_sampled(O):
+    """The same 65536 x 32 x 2^16 workload through the vectorised call, in the launch
+    configuration the benchmark times (default tiling, 1024 parents per call, each call's
+    output k-major: element g N Mv + k Mv + gamma). Checked: the first output of every
+    substream, every output of one substream per slice, and 32 sampled outputs plus the end
+    state of every substream of every 251st parent."""
+    cfg = workload.CONFIGS["split_65536x32x2^16"]
+    K, MV, N = cfg["instances"], cfg["substreams"], cfg["count"]
+    SL = 1024
+    ctx = R.Context(K + K * MV)
+    seeds = workload.instance_seeds(cfg["master"], K)
+    first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+    p, q, e, m0 = oracle_params(O, seeds, cfg)
+    out_c = torch.empty(SL * MV * N, dtype=torch.int64, device="cuda")
+    out_r = torch.empty(SL * MV * N, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(10)
+    s_start = np.array([O.split_s0(1, A, MV, g) for g in range(MV)], np.uint64)
+    for s0 in range(0, K, SL):
+        kids = np.stack([ctx.split(first + i, MV) for i in range(s0, s0 + SL)])
+        ctx.generate_interleaved(kids, N, out_r=out_r, out_c=out_c)
+        torch.cuda.synchronize()
+        # first output of every substream: elements g N Mv + gamma
+        idx = (torch.arange(SL, device="cuda").repeat_interleave(MV) * (N * MV)
+               + torch.arange(MV, device="cuda").repeat(SL))
+        g_c = out_c[idx].cpu().numpy().view(np.uint64)
+        g_r = out_r[idx].cpu().numpy()
+        inst = np.repeat(np.arange(s0, s0 + SL), MV)
+        gam = np.tile(np.arange(MV), SL)
+        want_c, want_r = O.sample_many(p[inst], q[inst], e[inst], np.full(len(inst), A, np.uint64),
+                                       m0[inst].copy(), s_start[gam].copy(), [[1]] * len(inst))
+        assert np.array_equal(g_c, want_c) and np.array_equal(bits(g_r), bits(want_r))
+        # one whole substream per slice: elements g N Mv + k Mv + gamma, k = 0..N-1
+        j = int(rng.integers(0, SL * MV))
+        i, g = s0 + j // MV, j % MV
+        c, r, _, _ = O.generate(int(p[i]), int(q[i]), int(e[i]), int(m0[i]),
+                                O.split_s0(1, A, MV, g), N, route=O.ROUTE_DIRECT)
+        sub = torch.arange(N, device="cuda") * MV + (j // MV) * N * MV + g
+        assert np.array_equal(out_c[sub].cpu().numpy().view(np.uint64), c)
+        assert np.array_equal(bits(out_r[sub].cpu().numpy()), bits(r))
+        # every 251st parent: sampled outputs and end states of all its substreams
+        for i in range(s0, s0 + SL):
+            if i % 251:
+                continue
+            ks = [np.unique(np.concatenate([rng.integers(1, N + 1, 31), [N]]))
+                  for _ in range(MV)]
+            m = np.full(MV, m0[i], np.uint64)
+            s = s_start.copy()
+            wc, wr = O.sample_many(np.full(MV, p[i]), np.full(MV, q[i]), np.full(MV, e[i]),
+                                   np.full(MV, A, np.uint64), m, s, ks)
+            base = (i - s0) * MV * N
+            gidx = np.concatenate([base + (k - 1) * MV + g for g, k in enumerate(ks)]).astype(np.int64)
+            t = torch.from_numpy(gidx).cuda()
+            assert np.array_equal(out_c[t].cpu().numpy().view(np.uint64), wc)
+            assert np.array_equal(bits(out_r[t].cpu().numpy()), bits(wr))
+            for g in range(MV):
+                assert ctx.get_state(int(kids[i - s0][g])) == (int(m[g]), int(s[g]))
+    ctx.close()
 
 
 def test_batched_full_size_graph(O):
