@@ -225,9 +225,25 @@ def check_vector(L):
     return True
 
 
+def check_seek_parallel(L):
+    # the skip sums split over threads (ranges started by jump-ahead) equal the serial walk
+    p, q = 2147483659, 4294967291
+    for a, s0, k in ((A, 7, 0), (A, 7, 1), (A, 7, 1000), (A, 99, 123457), (1, 99, 5000)):
+        prm = P(p, q, 3, a, Q)
+        out = []
+        for fn in (L.or_seek, L.or_seek_parallel):
+            m, s = ctypes.c_uint64(12345), ctypes.c_uint64(s0)
+            if fn(ctypes.byref(prm), ctypes.byref(m), ctypes.byref(s), k) != 0:
+                return False
+            out.append((m.value, s.value))
+        if out[0] != out[1]:
+            return False
+    return True
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
           check_rsa, check_unit, check_split, check_histogram, check_modes, check_unit_exact,
-          check_vector]
+          check_vector, check_seek_parallel]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -256,6 +272,8 @@ MUTANTS = {
     "crt_exponent_wrong_modulus": ("return ra + a * t;", "return ra + b * t;"),
     "exact_division_truncates": ("    if (round_bit && (sticky || (m & 1)))\n        m++;\n", ""),
     "vector_substream_major": ("                c_out[k * Mv + g] = c;", "                c_out[g * N + k] = c;"),
+    "parallel_seek_range_start": ("uint64_t s = or_mulmod(s0, or_powmod(a, lo, Q), Q);",
+                                  "uint64_t s = or_mulmod(s0, or_powmod(a, lo + 1, Q), Q);"),
 }
 
 
