@@ -344,6 +344,35 @@ int main(int argc, char **argv)
             }
         }
     }
+    // 7. the split workload's shapes (parents x 32 substreams x 2^16, 128 x 8 tiles, 760
+    // resident blocks): the vector units' last round is nearly full
+    for (uint32_t parents : {8u, 32u, 256u, 1024u, 4096u}) {
+        case_no++;
+        const uint32_t k = parents * 32;
+        std::vector<InstParams> P(k);
+        for (uint32_t i = 0; i < k; i++)
+            P[i].e = P[i].eq = 3 + 2 * ((i / 32) % 3);
+        std::vector<uint32_t> ids(k);
+        std::vector<uint64_t> cnt(k, 65536), off(k);
+        for (uint32_t i = 0; i < k; i++) {
+            ids[i] = i;
+            off[i] = (uint64_t)(i / 32) * 65536 * 32 + (i % 32);
+        }
+        const PlanGeometry geo{128, 8, 760};
+        HostPlan hp;
+        if (build_plan_core(P.data(), k, RSAPRNG_MODEXP_CRT32, geo, k, ids.data(), cnt.data(),
+                            off.data(), 0, hp, 1, 32) != RSAPRNG_OK) {
+            failures++;
+            continue;
+        }
+        const uint64_t u = hp.vecs.size(), rounds = (u + geo.grid - 1) / geo.grid;
+        const double fill = (double)u / (double)(rounds * geo.grid);
+        if (fill < 0.85) {
+            std::printf("split shape %u parents: %llu units, last round fill %.3f\n", parents,
+                        (unsigned long long)u, fill);
+            failures++;
+        }
+    }
     std::printf("%d cases, %d failures\n", case_no, failures);
     return failures ? 1 : 0;
 }
