@@ -279,12 +279,22 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
     cudaError_t e;
-    // The persistent launch's ticket is reset before the pre-pass, so that the
-    // three kernels follow one another directly (each a programmatic dependent
-    // of the one before).
-    if (dp.nitems && !fresh) {
-        if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
-            return cuda_fail(e, "ticket reset");
+    const bool vec = !hist && dp.stride > 1 && dp.nvecs;
+    GenLaunch g{};
+    if (dp.nitems) {
+        g = hist  ? hist_launch(c, cfg, dp.nitems)
+            : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr)
+                  : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
+        g.stride = dp.stride;
+        g.pdl = dp.nchunks > 0;
+        dp.last = g;
+        // A persistent launch's ticket is reset before the pre-pass, so that the
+        // kernels follow one another directly (each a programmatic dependent of
+        // the one before).
+        if (g.persistent && !fresh) {
+            if ((e = cudaMemsetAsync(dp.ticket, 0, sizeof(uint32_t), stream)) != cudaSuccess)
+                return cuda_fail(e, "ticket reset");
+        }
     }
     if (dp.nchunks) {
         if ((e = launch_prep_sums(t, dp.chunks, dp.nchunks, dp.chunk_sum, dp.chunk_s, stream)) !=
@@ -296,14 +306,6 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         nl += 2;
     }
     if (dp.nitems) {
-        const bool vec = !hist && dp.stride > 1 && dp.nvecs;
-        GenLaunch g = hist  ? hist_launch(c, cfg, dp.nitems)
-                      : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr)
-                            : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr,
-                                         &dp.occupancy);
-        g.stride = dp.stride;
-        g.pdl = dp.nchunks > 0;
-        dp.last = g;
         if (hist)
             e = launch_histogram(g, t, dp.items, dp.nitems, dp.ticket, *hist, stream);
         else if (vec)
