@@ -664,9 +664,6 @@ def run_ours(args) -> int:
     if not args.no_forms:
         # The plain, batched, served, fused and interleaved forms of the same path on this GPU.
         want = set(args.forms.split(","))
-        unknown = want - set(FORMS)
-        if unknown:
-            raise SystemExit(f"unknown forms: {sorted(unknown)}")
         lr, rk = dist.local_rank, dist.rank
         runs = (("plain_1x1e6", "plain", lambda: form_plain(R, torch, lr, peak_alu, rk)),
                 ("batched_1e5_lognormal", "batched",
@@ -744,6 +741,11 @@ def main(argv=None) -> int:
     args = parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("--steps must be >= 1 and --warmup >= 0")
+    unknown = set(args.forms.split(",")) - set(FORMS)
+    if unknown:
+        raise SystemExit(f"unknown forms: {sorted(unknown)} (known: {', '.join(FORMS)})")
+    if args.parents < 1:
+        raise SystemExit("--parents must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -80,3 +80,16 @@ def test_reference_arm_prints_contract_line(capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["config"]["workload"] == bench.WORKLOAD
+
+
+def test_bench_rejects_unknown_forms_before_any_work():
+    import pytest
+
+    import bench
+
+    with pytest.raises(SystemExit, match="unknown forms"):
+        bench.main(["--forms", "plain,bogus"])
+    with pytest.raises(SystemExit, match="--parents"):
+        bench.main(["--parents", "0"])
+    assert set(bench.FORMS) >= {"plain", "batched", "served", "fused", "interleaved",
+                                "split_full"}
