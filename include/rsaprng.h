@@ -399,7 +399,10 @@ int rsaprng_params_from_seed(uint64_t seed, int e_rule, uint64_t e_lo, uint64_t 
 
 /* The output step alone (Eq. CodeFloatingPointStep with the Sec. V guard):
  * d_r[k] = RN(RN(d_c[k]) / RN(n_id)), 1 - 2^-53 in place of 1.0, for k < N,
- * using division route `divide` (RSAPRNG_DIVIDE_*; AUTO = the context's);
+ * using division route `divide` (RSAPRNG_DIVIDE_*; AUTO = the context's;
+ * with RSAPRNG_DIVIDE_HYBRID element k takes the integer route when
+ * k mod 4 = 3 and the reciprocal route otherwise, as output k of a thread's
+ * run does in the generation kernels);
  * RN(d_c[k] / n_id) when the context's rounding is RSAPRNG_ROUND_EXACT.
  * d_c values must be < n of instance `id`. Asynchronous on `stream`. */
 int rsaprng_unit_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, const uint64_t *d_c,
@@ -417,8 +420,10 @@ int rsaprng_transfer_bytes(const rsaprng_ctx *ctx, uint64_t *h2d, uint64_t *d2h)
  * internal stream: kind 0 = 32-bit integer multiply-add issue rate
  * (result in G lane-ops/s), 1 = FP64 divide rate (G div/s), 2 = HBM write
  * bandwidth (GB/s) over `bytes` bytes, 3 = widening 32x32->64 multiply rate,
- * 4 = 32-bit high-half multiply rate, 5 = 32-bit Montgomery product rate
- * (3-5 in G per second). */
+ * 4 = 32-bit high-half multiply rate, 5 = 32-bit Montgomery product rate,
+ * 6 = FP64 fused multiply-add rate, 7 = unsigned 64-bit to double conversion
+ * rate, 8 = rate of the whole reciprocal output step (conversion, product,
+ * two FMAs, 1.0 guard) (3-8 in G per second, all lanes of the device). */
 int rsaprng_microbench(rsaprng_ctx *ctx, int kind, uint64_t bytes, double *result);
 
 const char *rsaprng_strerror(int code);

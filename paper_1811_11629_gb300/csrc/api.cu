@@ -946,6 +946,7 @@ int rsaprng_unit_f64(rsaprng_ctx *c, rsaprng_id id, uint64_t N, const uint64_t *
                                 c->cfg.rounding == RSAPRNG_ROUND_EXACT ? DIVIDE_EXACT
                                 : divide == RSAPRNG_DIVIDE_INT         ? DIVIDE_INT
                                 : divide == RSAPRNG_DIVIDE_FP64        ? DIVIDE_FP64
+                                : divide == RSAPRNG_DIVIDE_HYBRID      ? DIVIDE_HYBRID
                                                                        : DIVIDE_RECIP,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess)
@@ -977,6 +978,8 @@ int rsaprng_microbench(rsaprng_ctx *c, int kind, uint64_t bytes, double *result)
         }
     } else if (kind >= 3 && kind <= 5) {
         e = microbench_mul(kind - 3, result, st);
+    } else if (kind >= 6 && kind <= 8) {
+        e = microbench_fp64(kind - 6, result, st);
     } else {
         cudaStreamDestroy(st);
         return fail(RSAPRNG_ERR_ARG, "unknown microbenchmark %d", kind);

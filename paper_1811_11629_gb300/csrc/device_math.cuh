@@ -257,9 +257,14 @@ __device__ __forceinline__ double unit_fp64(u64 c, double dn)
 // per-instance correctly rounded reciprocal y = RN(1/N) (N = RN(n)),
 // q0 = RN(C y), the residual r = C - q0 N by one fused multiply-add, and the
 // corrected quotient RN(q0 + r y) (Markstein's division by an FMA correction
-// step, IBM J. Res. Dev. 34(1), 1990). The result was checked bit for bit
-// against the correctly rounded quotient on random and boundary cases; the
-// library's tests keep checking it against the oracle.
+// step, IBM J. Res. Dev. 34(1), 1990). Markstein's theorem needs q0 within
+// one ulp of C/N; RN(C y) can be up to 1.5 ulps off when C's significand is
+// below N's, but only where C/N is far from every midpoint between doubles,
+// and there the correction step's error is still far smaller than that
+// distance; near a midpoint q0 is always one of its two neighbours. So the
+// result is RN(C/N) for every C, N (the library's tests check this
+// exhaustively at reduced precision and on constructed near-midpoint
+// quotients at full precision).
 __device__ __forceinline__ double unit_recip(u64 c, double dn, double y)
 {
     const double C = __ull2double_rn(c);
@@ -395,11 +400,13 @@ __device__ __forceinline__ double unit_int(u64 c, const InstParams &P)
 
 // The same value as unit_int, usually without the exact division. With X =
 // Mc 2^11 and D = Mn 2^11 (both in [2^63, 2^64)) and v the invariant
-// reciprocal of D, A = X + hi64(X v) approximates (X / D) 2^64 from below with
-// an error under 3 units (the low 32x32 partial product of X v is omitted).
-// The 53-bit significand is A's top bits; the bits below it decide the
-// rounding, and only when they lie within 3 units of the halfway point can
-// the error change the decision: then the exact routine decides. Rounding c
+// reciprocal of D, A = X + hi64(X v) approximates T = (X / D) 2^64 from
+// below with an error T - A in [0, 3 + 2^-63): X + floor(X v / 2^64) lies in
+// (T - 2 - 2^-63, T], and omitting the low 32x32 partial product of X v can
+// lower it by one more. The 53-bit significand is A's top bits; the bits
+// below it (g) decide the rounding. With an error below 4 units, g <= half - 4
+// always rounds down and g > half always up; only g in [half - 3, half] is
+// undecided, and there the exact routine decides. Rounding c
 // to 53 bits uses the add-half-minus-one-plus-lsb rule (ties to even) on the
 // left-normalised c; c < n < 2^64 - 2^35, so the addition cannot wrap.
 __device__ __forceinline__ double unit_int_fast(u64 c, const InstParams &P)

@@ -349,6 +349,8 @@ const void *select_kernel(int L, int modexp, int divide, int threads)
 }
 
 // The output step alone: r[i] = RN(RN(c[i]) / RN(n)) with the 1.0 guard.
+// Element i takes the route of output i mod 4 of a thread's run, so the
+// hybrid route sends every fourth element through the integer division.
 template <int DIV>
 __global__ void k_unit(const InstParams *__restrict__ params, uint32_t id,
                        const u64 *__restrict__ c, double *__restrict__ r, u64 N)
@@ -356,7 +358,7 @@ __global__ void k_unit(const InstParams *__restrict__ params, uint32_t id,
     const InstParams P = params[id];
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-        r[i] = to_unit<DIV>(c[i], P, 0);
+        r[i] = to_unit<DIV>(c[i], P, (int)(i & 3));
 }
 
 // ---------------------------------------------------------------- microbenchmarks
@@ -428,6 +430,43 @@ __global__ void k_mb_ddiv(uint32_t iters, double seed, double *sink)
     }
     double acc = x[0] + x[1] + x[2] + x[3];
     if (acc == 1.2345)
+        sink[0] = acc;
+}
+
+// FP64 pipe shapes, 8 independent chains per thread: 0 = fused multiply-add,
+// 1 = unsigned 64-bit integer to double conversion, 2 = the whole reciprocal
+// output step (conversion, product, two FMAs and the 1.0 guard) as the
+// generation kernels run it. Each result feeds the next input of its chain
+// so that nothing is hoisted out of the loop; the integer feedback is a few
+// ALU instructions beside the FP64 ones.
+template <int S>
+__global__ void k_mb_fp64(uint32_t iters, u64 seed, double dn, double y, u64 *sink)
+{
+    u64 c[8];
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        c[j] = (seed + (u64)(threadIdx.x * 8 + j) * 0x9E3779B97F4A7C15ULL) >> 2;
+        x[j] = (double)(threadIdx.x * 8 + j) * 0x1p-20 + 1.0;
+    }
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if constexpr (S == 0) {
+                x[j] = __fma_rn(x[j], 0.99999999999, 1e-12);
+            } else if constexpr (S == 1) {
+                c[j] += (u64)__double_as_longlong(__ull2double_rn(c[j])) >> 12;
+            } else {
+                const double r = dev::unit_recip(c[j], dn, y);
+                c[j] = (c[j] + (u64)__double_as_longlong(r)) & 0x3FFFFFFFFFFFFFFFULL;
+            }
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        acc ^= c[j] ^ (u64)__double_as_longlong(x[j]);
+    if (acc == 0x123456789ULL)
         sink[0] = acc;
 }
 
@@ -566,8 +605,10 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
         k_unit<DIVIDE_EXACT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     else if (divide == DIVIDE_FP64)
         k_unit<DIVIDE_FP64><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
-    else if (divide == DIVIDE_RECIP || divide == DIVIDE_HYBRID)
+    else if (divide == DIVIDE_RECIP)
         k_unit<DIVIDE_RECIP><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
+    else if (divide == DIVIDE_HYBRID)
+        k_unit<DIVIDE_HYBRID><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     else
         k_unit<DIVIDE_INT><<<grid, 256, 0, stream>>>(t.params, id, c, r, N);
     return cudaGetLastError();
@@ -630,6 +671,32 @@ cudaError_t microbench_ddiv(double *gdiv, cudaStream_t stream)
     e = time_it([&] { k_mb_ddiv<<<grid, threads, 0, stream>>>(iters, 3.0, sink); }, stream, &ms);
     cudaFree(sink);
     *gdiv = (double)grid * threads * iters * 4 / (ms * 1e-3) / 1e9;
+    return e;
+}
+
+cudaError_t microbench_fp64(int shape, double *gops, cudaStream_t stream)
+{
+    u64 *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 64);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = num_sms();
+    const int grid = sms * 8, threads = 256;
+    const uint32_t iters = 1 << 10;
+    // a modulus just below 2^63 and its correctly rounded reciprocal
+    const double dn = 0x1.fffffffffffffp+62, y = 1.0 / dn;
+    float ms = 0;
+    if (shape == 0)
+        e = time_it([&] { k_mb_fp64<0><<<grid, threads, 0, stream>>>(iters, 99, dn, y, sink); },
+                    stream, &ms);
+    else if (shape == 1)
+        e = time_it([&] { k_mb_fp64<1><<<grid, threads, 0, stream>>>(iters, 99, dn, y, sink); },
+                    stream, &ms);
+    else
+        e = time_it([&] { k_mb_fp64<2><<<grid, threads, 0, stream>>>(iters, 99, dn, y, sink); },
+                    stream, &ms);
+    cudaFree(sink);
+    *gops = (double)grid * threads * iters * 8 / (ms * 1e-3) / 1e9;
     return e;
 }
 

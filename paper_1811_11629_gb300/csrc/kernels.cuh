@@ -107,6 +107,7 @@ cudaError_t launch_unit(const DeviceTables &t, uint32_t id, uint64_t N, const ui
 cudaError_t microbench_imad(double *gops, cudaStream_t stream);
 cudaError_t microbench_ddiv(double *gdiv, cudaStream_t stream);
 cudaError_t microbench_mul(int shape, double *gops, cudaStream_t stream);
+cudaError_t microbench_fp64(int shape, double *gops, cudaStream_t stream);
 cudaError_t microbench_write(void *buf, size_t bytes, double *gbs, cudaStream_t stream);
 
 // Kernel attribute query for occupancy-based grid sizing.

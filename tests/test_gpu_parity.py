@@ -249,6 +249,43 @@ def test_unit_step_random_and_edges(O, divide):
         assert (got < 1.0).all() and (got >= 0.0).all()
 
 
+@pytest.mark.parametrize("divide", [R.DIVIDE_RECIP, R.DIVIDE_INT, R.DIVIDE_HYBRID,
+                                    R.DIVIDE_FP64])
+def test_unit_step_near_midpoints(O, divide):
+    """The default reading RN(RN(c)/RN(n)) where a route could round the wrong way.
+
+    Sec. V, Eq. CodeFloatingPointStep. Ciphertexts are built so that RN(c)/RN(n)
+    lies next to a midpoint between neighbouring doubles (down to 2^-106
+    relative), for moduli at the edges of the range (just above 2^62, both
+    sides of 2^63, just below 2^64, the largest n) and three seeded ones, with
+    c both below 2^53 (exact conversion) and above it (rounded conversion).
+    Every route, element by element, against the oracle.
+    """
+    import division_cases as DC
+
+    ctx = R.Context(16)
+    mods = [(p, q) for p, q, _ in DC.EDGE_MODULI]
+    for s in workload.instance_seeds(23, 3):
+        p, q, _, _ = O.params_from_seed(int(s))
+        mods.append((p, q))
+    stream = torch.cuda.current_stream().cuda_stream
+    for k, (p, q) in enumerate(mods):
+        n = p * q
+        e = next(x for x in range(3, 999, 2) if math.gcd(x, (p - 1) * (q - 1)) == 1)
+        i = ctx.create(p, q, e, 1)
+        c = DC.near_midpoint_ciphertexts(n, seed=k)
+        assert len(c) >= 100000 and (c < (1 << 53)).any() and (c >= (1 << 53)).any()
+        dc = torch.from_numpy(c.view(np.int64)).cuda().view(torch.uint64)
+        dr = torch.empty(len(c), dtype=torch.float64, device="cuda")
+        assert ctx.L.rsaprng_unit_f64(ctx.h, i, len(c), dc.data_ptr(), dr.data_ptr(), divide,
+                                      stream) == 0
+        torch.cuda.synchronize()
+        want = O.unit_many(c, n)
+        got = dr.cpu().numpy()
+        bad = np.nonzero(bits(got) != bits(want))[0]
+        assert len(bad) == 0, f"n={n}: c={c[bad[:3]]} got={got[bad[:3]]} want={want[bad[:3]]}"
+
+
 def test_large_exponents(O):
     """Exponents up to 2^32 - 1 exercise the top-bit handling of the square-and-multiply loop."""
     ctx = R.Context(16)

@@ -241,9 +241,49 @@ def check_seek_parallel(L):
     return True
 
 
+def check_unit_hard(L):
+    # quotients next to midpoints between doubles (see division_cases)
+    import division_cases as DC
+
+    for k in (0, 3):
+        p, q, _ = DC.EDGE_MODULI[k]
+        n = p * q
+        for c in DC.near_midpoint_ciphertexts(n, t_max=63, seed=k)[::7]:
+            if L.or_unit(int(c), n) != DC.reference_unit(int(c), n):
+                return False
+    return True
+
+
+def check_sample(L):
+    # or_sample_many at 1-based indices equals the matching elements of or_generate
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    ptr = lambda x: x.ctypes.data_as(u64p)
+    ps, qs, es, N = [2147483659, 4294967291], [2147483693, 4294967279], [5, 7], 3000
+    ks_list = [np.array([1, 2, 3, 50, 51, 2999, 3000], np.uint64),
+               np.array([1, 1000, 1001, 1500], np.uint64)]
+    nk = np.array([len(k) for k in ks_list], np.uint64)
+    koff = np.array([0, len(ks_list[0])], np.uint64)
+    ks = np.concatenate(ks_list)
+    m, s = np.array([11, 22], np.uint64), np.array([1, 1], np.uint64)
+    c = np.zeros(len(ks), np.uint64)
+    r = np.zeros(len(ks), np.float64)
+    arr = lambda xs: np.array(xs, np.uint64)
+    if L.or_sample_many(2, ptr(arr(ps)), ptr(arr(qs)), ptr(arr(es)), ptr(arr([A, A])), Q, ptr(m),
+                        ptr(s), ptr(ks), ptr(koff), ptr(nk), ptr(c),
+                        r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) != 0:
+        return False
+    for g in range(2):
+        rc, cg, rg, _, _ = _gen(L, ps[g], qs[g], es[g], [11, 22][g], 1, N)
+        idx = ks_list[g].astype(np.int64) - 1
+        sl = slice(int(koff[g]), int(koff[g] + nk[g]))
+        if rc != 0 or not (c[sl] == cg[idx]).all() or not (r[sl] == rg[idx]).all():
+            return False
+    return True
+
+
 CHECKS = [check_primality, check_roots, check_skips, check_period_tiny_q, check_closed_form,
           check_rsa, check_unit, check_split, check_histogram, check_modes, check_unit_exact,
-          check_vector, check_seek_parallel]
+          check_vector, check_seek_parallel, check_unit_hard, check_sample]
 
 MUTANTS = {
     "schrage_negative_branch": ("return (s1 >= s2) ? (s1 - s2) : (s1 + (Q - s2));",
@@ -272,6 +312,9 @@ MUTANTS = {
     "crt_exponent_wrong_modulus": ("return ra + a * t;", "return ra + b * t;"),
     "exact_division_truncates": ("    if (round_bit && (sticky || (m & 1)))\n        m++;\n", ""),
     "vector_substream_major": ("                c_out[k * Mv + g] = c;", "                c_out[g * N + k] = c;"),
+    "sample_zero_based_index": ("int rc = or_seek(P, m_io, s_io, ks[j] - done);",
+                                "int rc = or_seek(P, m_io, s_io, ks[j] - done - 1);"),
+    "sample_position_not_kept": ("        done = ks[j];\n", "        done = ks[j] - 1;\n"),
     "parallel_seek_range_start": ("uint64_t s = or_mulmod(s0, or_powmod(a, lo, Q), Q);",
                                   "uint64_t s = or_mulmod(s0, or_powmod(a, lo + 1, Q), Q);"),
 }

@@ -261,6 +261,63 @@ def test_unit_conversion_exact_rounding(oracle_mod):
     assert differ > 100
 
 
+def test_unit_near_midpoints(oracle_mod):
+    """Eq. CodeFloatingPointStep at its hardest inputs: RN(c)/RN(n) next to a midpoint.
+
+    The oracle's (double)c / (double)n must equal Python's correctly rounded
+    integer division of the two correctly rounded conversions on ciphertexts
+    built to put the quotient within 2^-106 .. 2^-90 relative of a midpoint
+    between neighbouring doubles, for moduli at the edges of the range.
+    """
+    import division_cases as DC
+
+    O = oracle_mod
+    for k, (p, q, _) in enumerate(DC.EDGE_MODULI):
+        n = p * q
+        c = DC.near_midpoint_ciphertexts(n, seed=k)
+        assert len(c) >= 100000
+        want = np.array([DC.reference_unit(int(x), n) for x in c])
+        got = O.unit_many(c, n)
+        bad = np.nonzero(got.view(np.uint64) != want.view(np.uint64))[0]
+        assert len(bad) == 0, (n, c[bad[:3]])
+        # the construction really lands next to midpoints (odd significands of RN(n))
+        if DC.split_double(float(n))[0] & 1:
+            d = [DC.midpoint_distance_ulps(int(x), n) for x in c[::max(1, len(c) // 400)]]
+            assert np.mean(np.array(d) < 2.0**-40) > 0.75
+
+
+def test_sample_many_matches_generate(oracle_mod):
+    """The sampler behind every full-size check: output k (1-based) of or_sample_many is
+    element k - 1 of or_generate, and each instance ends at its last sampled output."""
+    O = oracle_mod
+    rng = np.random.default_rng(31)
+    inst = _random_instances(O, 5, seed=41, e_rule=1, e_lo=3, e_hi=65537)
+    N = 100000
+    ks_list, full = [], []
+    for j, (p, q, e, ms) in enumerate(inst):
+        n = p * q
+        c, r, m_end, s_end = O.generate(p, q, e, ms % n, 1, N, route=O.ROUTE_DIRECT)
+        pick = {1, 2, N} | set(int(x) for x in rng.integers(1, N + 1, 40)) | {777, 778, 779}
+        ks = np.array(sorted(pick)[: 10 + 8 * j], dtype=np.uint64)
+        ks_list.append(ks)
+        full.append((c, r))
+    arr = lambda i: np.array([x[i] for x in inst], dtype=np.uint64)
+    m = np.array([ms % (p * q) for p, q, _, ms in inst], dtype=np.uint64)
+    s = np.ones(len(inst), np.uint64)
+    a = np.full(len(inst), ROOTS[0], np.uint64)
+    c_s, r_s = O.sample_many(arr(0), arr(1), arr(2), a, m, s, ks_list)
+    off = 0
+    for j, (p, q, e, ms) in enumerate(inst):
+        ks = ks_list[j].astype(np.int64)
+        c, r = full[j]
+        assert (c_s[off:off + len(ks)] == c[ks - 1]).all()
+        assert (r_s[off:off + len(ks)].view(np.uint64) == r[ks - 1].view(np.uint64)).all()
+        off += len(ks)
+        _, _, m_last, s_last = O.generate(p, q, e, ms % (p * q), 1, int(ks[-1]),
+                                          route=O.ROUTE_DIRECT, want_c=False, want_r=False)
+        assert (int(m[j]), int(s[j])) == (m_last, s_last)
+
+
 def test_tiny_q_period_and_message_counts(oracle_mod):
     """Sec. IV: with a primitive root a mod Q' and gcd(Q'(Q'-1)/2, n) = 1 the period is
     (Q'-1) n and every message appears exactly Q'-1 times per period."""
