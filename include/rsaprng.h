@@ -203,8 +203,8 @@ int rsaprng_generate_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_
 int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
                           void *stream);
 
-/* The same as rsaprng_generate_f64, for callers that cannot allocate: code
- * running inside a CUDA stream capture, latency-critical threads that forbid
+/* The same as rsaprng_generate_f64, for callers that cannot allocate device
+ * memory when they draw numbers: latency-critical threads that forbid
  * allocator calls, or hosts that give all device memory to their own pool.
  * The paper has no counterpart; this is a deployment variant of the same
  * path. It allocates nothing: its scratch (chunk list, skip sums, work-queue
@@ -213,6 +213,10 @@ int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t 
  *  - Limit: N <= 2^36 outputs (at most 4096 chunks of at most 2^24 outputs);
  *    larger N returns RSAPRNG_ERR_ARG before anything is launched. Errors of
  *    this call return their code without setting rsaprng_last_error_detail.
+ *  - Also RSAPRNG_ERR_ARG: a context on a device index of 64 or more, and an
+ *    instance with CRT exponents when the context's route is
+ *    RSAPRNG_MODEXP_MONT64. The chunk length is chosen here (the context's
+ *    cfg.chunk is not used).
  *  - The first call on a device looks up the array's device address (one
  *    cudaGetSymbolAddress); make that first call before any stream capture.
  *  - All calls share the one array and it keeps the last call's contents

@@ -1,7 +1,6 @@
 // Generation without any allocation: rsaprng_generate_f64_noalloc.
 //
 // Some callers cannot allocate device memory at the time they want numbers:
-// code running inside a CUDA stream capture (where cudaMalloc is not allowed),
 // real-time or latency-critical threads that forbid allocator calls, and hosts
 // that hand all device memory to their own pool up front. The regular
 // generation calls may grow the context's work-list buffers with cudaMalloc on

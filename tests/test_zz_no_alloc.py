@@ -1,10 +1,10 @@
 """The allocation-free generation entry point (rsaprng_generate_f64_noalloc).
 
-It serves callers that cannot allocate device memory when they draw numbers
-(inside a stream capture, in threads that forbid allocator calls, or with all
-memory handed to an external pool). Through the C ABI, two calls in a row must
-give exactly the outputs of the regular rsaprng_generate_f64 on an identical
-instance (the tests' tolerance is zero: outputs are bit-exact).
+It serves callers that cannot allocate device memory when they draw numbers:
+threads with latency limits that forbid allocator calls, and hosts that hand
+all device memory to their own pool up front. Through the C ABI, calls in a
+row must give exactly the outputs of the regular rsaprng_generate_f64 on an
+identical instance (the tests' tolerance is zero: outputs are bit-exact).
 """
 import ctypes
 
@@ -31,7 +31,11 @@ def test_noalloc_matches_regular_entry_point_two_calls():
     a = ctx.create_ex(p, q, e, R.DEFAULT_ROOT, ms % n, 1)  # regular entry point
     b = ctx.create_ex(p, q, e, R.DEFAULT_ROOT, ms % n, 1)  # allocation-free entry point
     stream = torch.cuda.current_stream().cuda_stream
-    for N in (1_000_003, 4097):  # a multi-chunk call, then a short one continuing the stream
+    cfg = ctx.config()
+    tile = cfg["threads_per_block"] * cfg["numbers_per_thread"]
+    # a multi-chunk call, then short ones continuing the stream: a few chunks, then a
+    # single chunk (one output, exactly one tile) that takes its state from the table
+    for N in (1_000_003, 4097, 1, tile, tile - 1):
         want = torch.empty(N, dtype=torch.float64, device="cuda")
         got = torch.full((N + 1,), -1.0, dtype=torch.float64, device="cuda")
         assert L.rsaprng_generate_f64(ctx.h, a, N, want.data_ptr(), stream) == 0
