@@ -204,6 +204,59 @@ def imad_slots_per_number(e: int) -> int:
     return 5 * (2 * k + 1) + 6 + 5 + 2
 
 
+# Library microbenchmarks behind the roofline peaks (rsaprng_microbench kinds).
+MICROBENCH = {"imad": 0, "ddiv": 1, "imad_wide": 3, "imad_hi": 4, "mont32": 5, "dfma": 6,
+              "cvt_u64_f64": 7, "recip_step": 8}
+DIVIDE_RECIP, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID = 4, 1, 2, 3
+
+
+def measure_peaks(ctx, torch, device: int) -> dict:
+    """Device-wide rates (G per second, all lanes) measured by the library's own
+    microbenchmarks in this process, plus the unit counts the nominal figures use."""
+    rates = {name: round(ctx.microbench(kind), 2) for name, kind in MICROBENCH.items()}
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(device)
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    return {"rates_G_per_s": rates, "sms": props.multi_processor_count, "sm_max_mhz": sm_max,
+            "hbm_gbs": float(peaks.get("hbm_gbs") or 6800.0),
+            "hbm_source": "MEASURED_PEAKS.json hbm_gbs (copy)" if peaks.get("hbm_gbs")
+            else "fallback 6.8 TB/s",
+            "nominal_alu_slots": props.multi_processor_count * 64 * sm_max * 1e6 / 1e9}
+
+
+def fp64_route_rate(pk: dict, divide: int):
+    """Outputs per second (G) the FP64 pipe allows for a division route, or None when
+    the route does not use it (the integer route)."""
+    r = pk["rates_G_per_s"]
+    if divide == DIVIDE_RECIP:
+        return r["recip_step"]
+    if divide == DIVIDE_HYBRID:
+        return r["recip_step"] / 0.75  # three outputs in four
+    if divide == DIVIDE_FP64:
+        return 1.0 / (1.0 / r["ddiv"] + 1.0 / r["cvt_u64_f64"])
+    return None
+
+
+def bounds(pk: dict, numbers: float, slots: float, seconds: float, divide: int,
+           bytes_per_number: int) -> dict:
+    """The three bounds of one timed form: the integer-multiply pipe (algorithmic IMAD
+    slots per output, as Montgomery-product equivalents of 5 slots, against the measured
+    Montgomery-product rate), the FP64 pipe (the division route's measured step rate) and
+    HBM (output bytes against the measured copy bandwidth). frac is that of the binding one."""
+    rate = numbers / seconds / 1e9
+    out = {"alu_frac": round(slots / 5 / seconds / 1e9 / pk["rates_G_per_s"]["mont32"], 4),
+           "alu_frac_nominal": round(slots / seconds / 1e9 / pk["nominal_alu_slots"], 4),
+           "hbm_frac": round(rate * bytes_per_number / pk["hbm_gbs"], 4)}
+    fr = fp64_route_rate(pk, divide)
+    out["fp64_frac"] = round(rate / fr, 4) if fr else None
+    cand = {"alu": out["alu_frac"], "hbm": out["hbm_frac"]}
+    if fr:
+        cand["fp64"] = out["fp64_frac"]
+    out["bound"] = max(cand, key=cand.get)
+    out["frac"] = cand[out["bound"]]
+    return out
+
+
 KERNEL_SOURCES = ["paper_1811_11629_gb300/csrc/kernels.cu",
                   "paper_1811_11629_gb300/csrc/device_math.cuh",
                   "paper_1811_11629_gb300/csrc/kernels.cuh",
@@ -276,11 +329,15 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
 
 
 # --------------------------------------------------------------------------- other forms
+TUNED_KEYS = ("modexp", "divide", "threads_per_block", "numbers_per_thread", "blocks_per_sm",
+              "chunk", "streams_per_block", "unroll")
+
+
 def _slots(es, counts) -> float:
     return float(sum(imad_slots_per_number(int(e)) * int(c) for e, c in zip(es, counts)))
 
 
-def form_plain(R, torch, device, peak_alu, rank) -> dict:
+def form_plain(R, torch, device, pk, rank) -> dict:
     """Plain method: one instance, 1e6 outputs as uint64 c_k and float64 r_k per call."""
     cfg = workload.CONFIGS["plain_1x1e6"]
     ctx = R.Context(4, device=device)
@@ -300,10 +357,11 @@ def form_plain(R, torch, device, peak_alu, rank) -> dict:
     torch.cuda.synchronize()
     dt = a.elapsed_time(b) / 1e3 / reps
     e = ctx.params(first)[2]
+    divide = ctx.config()["divide"]
     out = {"value": round(n / dt / 1e9, 3), "unit": UNIT, "ms_per_call": round(dt * 1e3, 4),
-           "e": e, "outputs": "u64+f64",
-           "alu_frac": round(_slots([e], [n]) / dt / 1e9 / peak_alu, 4),
+           "e": e, "outputs": "u64+f64", "divide": divide,
            "hbm_GBps": round(16 * n / dt / 1e9, 1)}
+    out.update(bounds(pk, n, _slots([e], [n]), dt, divide, 16))
     # The same draw as a plan captured in a CUDA graph (one graph launch per 1e6 outputs).
     plan = ctx.plan([first], [n])
     st = torch.cuda.Stream()
@@ -318,13 +376,14 @@ def form_plain(R, torch, device, peak_alu, rank) -> dict:
     torch.cuda.synchronize()
     dt = a.elapsed_time(b) / 1e3 / reps
     out["graph"] = {"value": round(n / dt / 1e9, 3), "ms_per_call": round(dt * 1e3, 4),
-                    "api": "rsaprng_plan_capture + rsaprng_plan_replay"}
+                    "api": "rsaprng_plan_capture + rsaprng_plan_replay",
+                    **bounds(pk, n, _slots([e], [n]), dt, divide, 16)}
     plan.close()
     ctx.close()
     return out
 
 
-def form_batched(R, torch, device, peak_alu, rank) -> dict:
+def form_batched(R, torch, device, pk, rank) -> dict:
     """Batched uneven: 1e5 instances, lognormal lengths (~2^32 outputs, f64), one plan in a
     CUDA graph after autotuning on a 2000-instance sample."""
     cfg = workload.CONFIGS["batched_1e5_lognormal"]
@@ -354,9 +413,8 @@ def form_batched(R, torch, device, peak_alu, rank) -> dict:
     res = {"value": round(total / dt / 1e9, 3), "unit": UNIT, "ms_per_replay": round(dt * 1e3, 3),
            "numbers": total, "launches_per_replay": plan.info()["launches"],
            "chunks": plan.info()["chunks"],
-           "alu_frac": round(_slots(es, lens) / dt / 1e9 / peak_alu, 4),
-           "tuned": {x: tuned[x] for x in ("modexp", "divide", "threads_per_block",
-                                           "numbers_per_thread")}}
+           "tuned": {x: tuned[x] for x in TUNED_KEYS if x in tuned}}
+    res.update(bounds(pk, total, _slots(es, lens), dt, ctx.config()["divide"], 8))
     plan.close()
     del out
     ctx.close()
@@ -364,7 +422,7 @@ def form_batched(R, torch, device, peak_alu, rank) -> dict:
     return res
 
 
-def form_fused(R, torch, device, peak_alu, rank, k=0, n=0) -> dict:
+def form_fused(R, torch, device, pk, rank, k=0, n=0) -> dict:
     """Fused consumer: the bulk workload (1024 x 2^20, e uniform in [3, 65537]) binned into
     the frequency-test histogram (D = 1, 2^20 bins) and the serial-test histogram (D = 2,
     1024^2 bins) inside the generation kernel; nothing is written per output. k and n
@@ -393,14 +451,14 @@ def form_fused(R, torch, device, peak_alu, rank, k=0, n=0) -> dict:
         chi2, tuples = R.chi2_uniform(hist)
         out[name] = {"value": round(k * n / dt / 1e9, 3), "unit": UNIT,
                      "ms_per_call": round(dt * 1e3, 3),
-                     "alu_frac": round(_slots(es, [n] * k) / dt / 1e9 / peak_alu, 4),
-                     "chi2_per_dof": round(chi2 / (d ** D - 1), 5), "tuples": tuples}
+                     "chi2_per_dof": round(chi2 / (d ** D - 1), 5), "tuples": tuples,
+                     **bounds(pk, k * n, _slots(es, [n] * k), dt, ctx.config()["divide"], 0)}
         del hist
     ctx.close()
     return out
 
 
-def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> dict:
+def form_interleaved(R, torch, device, pk, rank, parents: int = 1024) -> dict:
     """The vectorised call of Sec. VI: a slice of the split workload (parents x 32 substreams
     x 2^16, e = 3 or the next valid odd, u64 + f64), every parent's k-major vector in one
     call; the substream-major batch over the same children is timed beside it."""
@@ -415,6 +473,8 @@ def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> d
     orr = torch.empty(parents * per, dtype=torch.float64, device="cuda")
 
     groups = np.stack(kids).astype(np.uint32)
+    slots = _slots([ctx.params(first + i)[2] for i in range(parents)], [per] * parents)
+    divide = ctx.config()["divide"]
 
     def vector_calls():
         ctx.generate_interleaved(groups, n, out_r=orr, out_c=oc)
@@ -433,7 +493,8 @@ def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> d
         torch.cuda.synchronize()
         dt = a.elapsed_time(b) / 1e3
         out[name] = {"value": round(parents * per / dt / 1e9, 3), "unit": UNIT,
-                     "ms": round(dt * 1e3, 2), "hbm_GBps": round(16 * parents * per / dt / 1e9, 1)}
+                     "ms": round(dt * 1e3, 2), "hbm_GBps": round(16 * parents * per / dt / 1e9, 1),
+                     **bounds(pk, parents * per, slots, dt, divide, 16)}
     out["shape"] = f"{parents} parents x {mv} substreams x {n}, u64 + f64, one call"
     ctx.close()
     del oc, orr
@@ -441,7 +502,7 @@ def form_interleaved(R, torch, device, peak_alu, rank, parents: int = 1024) -> d
     return out
 
 
-def form_split_full(R, torch, device, peak_alu, rank, slice_parents: int = 1024) -> dict:
+def form_split_full(R, torch, device, pk, rank, slice_parents: int = 1024) -> dict:
     """The whole split workload: 65536 parents x 32 substreams x 2^16 (2^37 outputs, u64 +
     f64 = 2 TiB, more than HBM holds), generated in slices of slice_parents parents into one
     reused output buffer; throughput over all slices, substream-major and interleaved."""
@@ -455,6 +516,8 @@ def form_split_full(R, torch, device, peak_alu, rank, slice_parents: int = 1024)
     oc = torch.empty(per, dtype=torch.int64, device="cuda")
     orr = torch.empty(per, dtype=torch.float64, device="cuda")
     counts = np.full(slice_parents * mv, n, np.uint64)
+    slots = _slots([ctx.params(first + i)[2] for i in range(parents)], [mv * n] * parents)
+    divide = ctx.config()["divide"]
 
     def substream_major(s):
         ctx.generate_batch(kids[s:s + slice_parents].reshape(-1), counts, out_r=orr, out_c=oc)
@@ -473,7 +536,8 @@ def form_split_full(R, torch, device, peak_alu, rank, slice_parents: int = 1024)
         torch.cuda.synchronize()
         dt = a.elapsed_time(b) / 1e3
         out[name] = {"value": round(parents * mv * n / dt / 1e9, 3), "unit": UNIT,
-                     "s": round(dt, 3), "hbm_GBps": round(16 * parents * mv * n / dt / 1e9, 1)}
+                     "s": round(dt, 3), "hbm_GBps": round(16 * parents * mv * n / dt / 1e9, 1),
+                     **bounds(pk, parents * mv * n, slots, dt, divide, 16)}
     out["shape"] = (f"{parents} parents x {mv} substreams x {n} = 2^37 outputs, u64 + f64, "
                     f"{parents // slice_parents} slices of {slice_parents} parents into one "
                     f"{16 * per // 2**30} GiB buffer")
@@ -483,7 +547,7 @@ def form_split_full(R, torch, device, peak_alu, rank, slice_parents: int = 1024)
     return out
 
 
-def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dict:
+def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
     [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
     cfg = workload.CONFIGS["serving_1e6"]
@@ -515,6 +579,7 @@ def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dic
                        "iterations": st["iterations"]})
     es = [ctx.params(int(i))[2] for i in pick[:200]]
     mean_slots = float(np.mean([imad_slots_per_number(int(e)) for e in es]))
+    divide = ctx.config()["divide"]
     srv.close()
     ctx.close()
     torch.cuda.empty_cache()
@@ -522,10 +587,9 @@ def form_served(R, torch, device, peak_alu, rank, loads=(0.25, 0.5, 0.9)) -> dic
     return {"value": round(cap_numbers / 1e9, 3), "unit": UNIT,
             "capacity_req_per_s": round(cap_rate, 1), "requests_per_point": nreq,
             "mean_count": round(mean_cnt, 1), "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
-            "at_load": mid["load"], "alu_frac": round(cap_numbers * mean_slots / 1e9 / peak_alu, 4),
-            "tuned": {x: tuned[x] for x in ("modexp", "divide", "threads_per_block",
-                                            "numbers_per_thread")},
-            "points": points}
+            "at_load": mid["load"],
+            "tuned": {x: tuned[x] for x in TUNED_KEYS if x in tuned},
+            "points": points, **bounds(pk, cap_numbers, cap_numbers * mean_slots, 1.0, divide, 8)}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -557,6 +621,7 @@ def run_ours(args) -> int:
     ids = np.arange(first, first + k, dtype=np.uint32)
     counts = np.full(k, n, np.uint64)
     es = [ctx.params(int(i))[2] for i in ids]
+    pk = measure_peaks(ctx, torch, dist.local_rank)
     tuned = None
     if args.tune:
         tuned = ctx.autotune(ids, counts, reps=1)
@@ -594,15 +659,29 @@ def run_ours(args) -> int:
     total_numbers = dist.sum(float(numbers_per_step * args.steps))
     value = total_numbers / elapsed_max / 1e9
 
-    # Roofline of the generation kernel (one launch per step, plus a 4-byte ticket reset).
+    # Roofline of the generation kernel (one launch per step, plus a 4-byte ticket reset):
+    # three bounds, each against a rate measured in this process (see measure_peaks).
     kern_s = statistics.mean(step_ms) / 1e3
     ops = sum(imad_slots_per_number(int(e)) for e in es) * n
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    peak_alu = 152 * 64 * sm_max * 1e6 / 1e9  # G IMAD slots/s: 152 SMs x 64 lanes/clk
-    achieved = ops / kern_s / 1e9
-    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
-    hbm_achieved = numbers_per_step * 8 / kern_s / 1e9
+    cur = ctx.config()
+    b = bounds(pk, numbers_per_step, ops, kern_s, cur["divide"], 8)
+    rates = pk["rates_G_per_s"]
+    fp64_rate = fp64_route_rate(pk, cur["divide"])
+    per_bound = {
+        "alu": {"achieved": round(ops / 5 / kern_s / 1e9, 2), "peak": rates["mont32"],
+                "unit": "G Montgomery-product equivalents/s", "frac": b["alu_frac"],
+                "op": "5 integer-multiply-pipe slots (IMAD = 1, IMAD.HI / IMAD.WIDE = 2), the "
+                      "cost of one 32-bit Montgomery product",
+                "ops_per_step": ops / 5,
+                "peak_source": "measured: rsaprng_microbench 32-bit Montgomery product rate"},
+        "fp64": {"achieved": round(numbers_per_step / kern_s / 1e9, 2),
+                 "peak": round(fp64_rate, 2) if fp64_rate else None,
+                 "unit": "G output steps/s", "frac": b["fp64_frac"],
+                 "op": "the division route's output step on the FP64 pipe",
+                 "peak_source": "measured: rsaprng_microbench output-step rate of the route"},
+        "hbm": {"achieved": round(numbers_per_step * 8 / kern_s / 1e9, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": b["hbm_frac"], "peak_source": pk["hbm_source"]}}
+    top = per_bound[b["bound"]]
 
     result = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world,
@@ -614,26 +693,20 @@ def run_ours(args) -> int:
                    "e": "uniform over valid odd values in [3, 65537]", "output": "float64",
                    "one_instance_per_block": True, "parallelism": f"instances x{dist.world}",
                    "l2": "outputs 8 GiB per step > L2: no flush"},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
-                     "unit": "Gop/s", "frac": round(achieved / peak_alu, 4), "traffic": None,
-                     "op": "integer-multiply pipe slot (IMAD = 1, IMAD.HI / IMAD.WIDE = 2) per lane",
-                     "ops_per_step": ops,
-                     "peak_source": "152 SMs x 64 IMAD lanes/clk x sm_max (nominal unit count)",
-                     "kernel_ms": round(kern_s * 1e3, 3),
-                     "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak,
-                             "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4),
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks.get("hbm_gbs")
-                             else "fallback"}},
+        "roofline": {"bound": b["bound"], "achieved": top["achieved"], "peak": top["peak"],
+                     "unit": top["unit"], "frac": b["frac"], "traffic": None,
+                     "kernel_ms": round(kern_s * 1e3, 3), "bounds": per_bound,
+                     "nominal": {"alu_slots_peak": round(pk["nominal_alu_slots"], 1),
+                                 "alu_frac": b["alu_frac_nominal"],
+                                 "source": f"{pk['sms']} SMs x 64 IMAD lanes/clk x "
+                                           f"{pk['sm_max_mhz']:.0f} MHz (unit counts)"},
+                     "rates_measured_G_per_s": rates},
         "gpu_launches": gpu_launches,
         "clocks": clk,
     }
     if tuned:
-        result["config"]["tuned"] = {x: tuned[x] for x in ("modexp", "divide",
-                                                           "threads_per_block",
-                                                           "numbers_per_thread")}
-    cur = ctx.config()
-    result["config"]["kernel"] = {x: cur[x] for x in ("modexp", "divide", "threads_per_block",
-                                                      "numbers_per_thread")}
+        result["config"]["tuned"] = {x: tuned[x] for x in TUNED_KEYS if x in tuned}
+    result["config"]["kernel"] = {x: cur[x] for x in TUNED_KEYS if x in cur}
     result["config"]["kernel"].update(plan.shape())
     if (k, n) == (workload.CONFIGS[WORKLOAD]["instances"], workload.CONFIGS[WORKLOAD]["count"]):
         result["roofline"]["traffic"] = measured_traffic(result["config"]["kernel"])
@@ -665,16 +738,16 @@ def run_ours(args) -> int:
         # The plain, batched, served, fused and interleaved forms of the same path on this GPU.
         want = set(args.forms.split(","))
         lr, rk = dist.local_rank, dist.rank
-        runs = (("plain_1x1e6", "plain", lambda: form_plain(R, torch, lr, peak_alu, rk)),
+        runs = (("plain_1x1e6", "plain", lambda: form_plain(R, torch, lr, pk, rk)),
                 ("batched_1e5_lognormal", "batched",
-                 lambda: form_batched(R, torch, lr, peak_alu, rk)),
-                ("serving_1e6", "served", lambda: form_served(R, torch, lr, peak_alu, rk)),
+                 lambda: form_batched(R, torch, lr, pk, rk)),
+                ("serving_1e6", "served", lambda: form_served(R, torch, lr, pk, rk)),
                 ("fused_histogram_bulk", "fused",
-                 lambda: form_fused(R, torch, lr, peak_alu, rk, args.instances, args.count)),
+                 lambda: form_fused(R, torch, lr, pk, rk, args.instances, args.count)),
                 ("split_interleaved", "interleaved",
-                 lambda: form_interleaved(R, torch, lr, peak_alu, rk, parents=args.parents)),
+                 lambda: form_interleaved(R, torch, lr, pk, rk, parents=args.parents)),
                 ("split_full_65536x32x2^16", "split_full",
-                 lambda: form_split_full(R, torch, lr, peak_alu, rk)))
+                 lambda: form_split_full(R, torch, lr, pk, rk)))
         result["forms"] = {name: fn() for name, key, fn in runs if key in want}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)

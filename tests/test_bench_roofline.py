@@ -33,3 +33,30 @@ def test_bulk_average():
           for s in seeds]
     mean = float(np.mean([bench.imad_slots_per_number(int(e)) for e in es]))
     assert abs(mean - 243.5) < 0.5
+
+
+def _fake_peaks():
+    return {"rates_G_per_s": {"mont32": 3500.0, "recip_step": 160.0, "ddiv": 70.0,
+                              "cvt_u64_f64": 300.0},
+            "hbm_gbs": 6800.0, "nominal_alu_slots": 20000.0}
+
+
+def test_bounds_pick_the_binding_unit():
+    pk = _fake_peaks()
+    # bulk-like: 2^30 outputs, 243.5 slots each, 19.7 ms -> the multiply pipe binds
+    b = bench.bounds(pk, 2**30, 243.5 * 2**30, 0.0197, bench.DIVIDE_RECIP, 8)
+    assert b["bound"] == "alu"
+    assert abs(b["alu_frac"] - 243.5 * 2**30 / 5 / 0.0197 / 1e9 / 3500.0) < 1e-4
+    assert b["frac"] == max(b["alu_frac"], b["fp64_frac"], b["hbm_frac"])
+    # e = 3 (48 slots): 120 G outputs/s -> the reciprocal step on the FP64 pipe binds
+    b = bench.bounds(pk, 120e9, 48 * 120e9, 1.0, bench.DIVIDE_RECIP, 16)
+    assert b["bound"] == "fp64" and abs(b["fp64_frac"] - 0.75) < 1e-9
+    # the integer route has no FP64 bound; the hybrid route puts 3 of 4 outputs on it
+    assert bench.bounds(pk, 120e9, 48 * 120e9, 1.0, bench.DIVIDE_INT, 16)["fp64_frac"] is None
+    h = bench.bounds(pk, 120e9, 48 * 120e9, 1.0, bench.DIVIDE_HYBRID, 16)
+    assert abs(h["fp64_frac"] - 0.75 * 0.75) < 1e-9
+    # IEEE division: division and conversion rates in series
+    f = bench.bounds(pk, 10e9, 0, 1.0, bench.DIVIDE_FP64, 0)
+    assert abs(f["fp64_frac"] - 10 * (1 / 70 + 1 / 300)) < 1e-4
+    # nothing stored: no HBM work
+    assert f["hbm_frac"] == 0.0
