@@ -362,6 +362,22 @@ def form_plain(R, torch, device, pk, rank) -> dict:
            "e": e, "outputs": "u64+f64", "divide": divide,
            "hbm_GBps": round(16 * n / dt / 1e9, 1)}
     out.update(bounds(pk, n, _slots([e], [n]), dt, divide, 16))
+    out["path"] = "one launch, decoupled look-back over the tiles' skip sums"
+    # The same calls through the chunked path (skip-sum pre-pass, scan, generation).
+    ctx.configure(lookback=R.LOOKBACK_OFF)
+    for _ in range(3):
+        ctx.generate_both(first, n, oc, orr)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ctx.generate_both(first, n, oc, orr)
+    b.record()
+    torch.cuda.synchronize()
+    dtc = a.elapsed_time(b) / 1e3 / reps
+    out["chunked"] = {"value": round(n / dtc / 1e9, 3), "ms_per_call": round(dtc * 1e3, 4),
+                      "path": "pre-pass + scan + generation (three launches)"}
+    ctx.configure()
+    assert ctx.device_status() == 0
     # The same draw as a plan captured in a CUDA graph (one graph launch per 1e6 outputs).
     plan = ctx.plan([first], [n])
     st = torch.cuda.Stream()

@@ -119,8 +119,28 @@ typedef struct {
     int32_t require_safe;       /* p, q must be safe primes (Sec. V) */
     int32_t rounding;           /* RSAPRNG_ROUND_*; with RSAPRNG_ROUND_EXACT the divide
                                    route is ignored (one integer route computes it) */
-    int32_t reserved[6];
+    int32_t lookback;           /* RSAPRNG_LOOKBACK_*: how the one-instance calls
+                                   (rsaprng_generate_u64/f64/both) run */
+    int32_t spin_limit;         /* empty poll rounds (64 ns apart) before a device-side
+                                   wait gives up and raises the device error flag;
+                                   0 = default (2^23, about a second), < 0 = none
+                                   (give up at the first empty round; tests) */
+    int32_t test_flags;         /* 0 in normal use. Bit 0: the first tile of a
+                                   single-launch call publishes no prefix, so every
+                                   later tile's wait runs out (tests of the device
+                                   error path; no GPU fault is involved) */
+    int32_t reserved[3];
 } rsaprng_config;
+
+enum {
+    RSAPRNG_LOOKBACK_AUTO = 0, /* one launch with a decoupled look-back when the draw is
+                                  at most 4096 tiles and the tiling has such a kernel
+                                  (16 per thread on the CRT route, 8 per thread on the
+                                  CRT route with reciprocal division or on the 64-bit
+                                  route with reciprocal or integer division); else the
+                                  chunked path (skip-sum pre-pass, scan, generation) */
+    RSAPRNG_LOOKBACK_OFF = 1   /* always the chunked path */
+};
 
 /* ------------------------------------------------------------- context */
 
@@ -195,9 +215,13 @@ int rsaprng_get_params(rsaprng_ctx *ctx, rsaprng_id id, uint64_t *p, uint64_t *q
 /* ---------------------------------------------------------- generation */
 
 /* N outputs of one instance into caller device buffers (Eq. algorithm1):
- * d_c[k] = c_{k+1}, d_r[k] = r_{k+1}; advances the instance by N. Long
- * streams are cut into chunks whose start states come from an on-device
- * skip-sum pass, so the whole GPU works on one instance. */
+ * d_c[k] = c_{k+1}, d_r[k] = r_{k+1}; advances the instance by N. A draw of
+ * at most 4096 tiles runs as one launch: block b generates tile b and gets
+ * the message before it (Sec. IV: m_0 plus the skips before it, mod n) by a
+ * decoupled look-back over the earlier tiles' skip sums, every wait bounded
+ * by cfg.spin_limit (see rsaprng_device_status). Longer draws are cut into
+ * chunks whose start states come from an on-device skip-sum pass and scan.
+ * Either way the whole GPU works on one instance. */
 int rsaprng_generate_u64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, void *stream);
 int rsaprng_generate_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_r, void *stream);
 int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
@@ -335,6 +359,12 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms, max_ms; /* arrival -> completion latency */
     double busy_s, wall_s;                  /* device-busy and wall time */
     uint64_t iterations;                    /* batched launches issued */
+    uint64_t max_inflight_iterations;       /* most iterations in flight at once
+                                               (launched, not yet retired) */
+    uint64_t overlapped_iterations;         /* iterations whose device interval (events
+                                               on their stream before the plan upload and
+                                               after the launch) overlapped the interval
+                                               of another iteration */
 } rsaprng_stats;
 
 /* A continuous-batching request server over the context's instances. It owns
@@ -371,6 +401,14 @@ int rsaprng_server_stats(rsaprng_server *srv, rsaprng_stats *out);
 int rsaprng_server_replay(rsaprng_server *srv, uint64_t n, const rsaprng_id *ids,
                           const uint64_t *counts, const uint64_t *arrival_ns,
                           uint64_t timeout_ns, double *lat_ms_out);
+/* The same replay with every result kept: tickets_out[i] (a HOST array of n)
+ * receives request i's ticket, whose outputs stay in the arena until the
+ * caller reads them (rsaprng_server_result / _copy) and releases them, so the
+ * budget must hold all n results. Used to check results of requests that
+ * arrived while others were running. */
+int rsaprng_server_replay_keep(rsaprng_server *srv, uint64_t n, const rsaprng_id *ids,
+                               const uint64_t *counts, const uint64_t *arrival_ns,
+                               uint64_t timeout_ns, uint64_t *tickets_out);
 void rsaprng_server_destroy(rsaprng_server *srv);
 
 /* ------------------------------------------------------- host utilities */
@@ -411,6 +449,15 @@ int rsaprng_params_from_seed(uint64_t seed, int e_rule, uint64_t e_lo, uint64_t 
  * d_c values must be < n of instance `id`. Asynchronous on `stream`. */
 int rsaprng_unit_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, const uint64_t *d_c,
                      double *d_r, int divide, void *stream);
+
+/* Waits for `stream`, then reads and clears the context's device error word.
+ * Returns RSAPRNG_ERR_DEVICE_FLAG if a device-side wait gave up since the last
+ * call (a single-launch draw whose tile never received its predecessors'
+ * prefix within spin_limit polls; that draw's outputs and the instance's
+ * state are then undefined: restore it with rsaprng_set_state), else
+ * RSAPRNG_OK. The paper has no counterpart (failure detection of this
+ * library's own waits). */
+int rsaprng_device_status(rsaprng_ctx *ctx, void *stream);
 
 /* Kernel launches issued by this context so far (for launch accounting). */
 uint64_t rsaprng_launch_count(const rsaprng_ctx *ctx);

@@ -12,13 +12,13 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DEFAULT_ROOT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_INT, DIVIDE_RECIP, E_AT_LEAST, E_SMALLEST, E_UNIFORM,
-                   HIST_HIGH, HIST_LOW,
+                   HIST_HIGH, HIST_LOW, LOOKBACK_AUTO, LOOKBACK_OFF,
                    MODEXP_CRT32, MODEXP_MONT64, Q, Config, RsaPrngError, Stats, check)
 
 __all__ = ["Context", "Plan", "Server", "Config", "RsaPrngError", "is_prime", "root_allowed",
            "params_from_seed", "Q", "DEFAULT_ROOT", "MODEXP_CRT32", "MODEXP_MONT64",
            "DIVIDE_INT", "DIVIDE_FP64", "DIVIDE_HYBRID", "DIVIDE_RECIP", "E_SMALLEST", "E_UNIFORM", "E_AT_LEAST",
-           "HIST_HIGH", "HIST_LOW", "chi2_uniform"]
+           "HIST_HIGH", "HIST_LOW", "LOOKBACK_AUTO", "LOOKBACK_OFF", "chi2_uniform"]
 
 
 def _u64p(a: np.ndarray):
@@ -215,6 +215,11 @@ class Context:
     def generate_both(self, id_, n, out_c, out_r, stream=None):
         check(self.L.rsaprng_generate_both(self.h, id_, n, _dptr(out_c), _dptr(out_r),
                                            _stream_ptr(stream)), "generate_both")
+
+    def device_status(self, stream=None) -> int:
+        """Waits for the stream; returns the status code of rsaprng_device_status
+        (0, or the device-flag error when a device-side wait gave up) and clears it."""
+        return self.L.rsaprng_device_status(self.h, _stream_ptr(stream))
 
     @staticmethod
     def _req(ids, counts, offsets):
@@ -418,6 +423,18 @@ class Server:
                                            _u64p(arr), int(timeout_s * 1e9),
                                            lat.ctypes.data_as(_lib.pdbl)), "server_replay")
         return lat
+
+    def replay_keep(self, ids, counts, arrival_s, timeout_s: float = 600.0) -> np.ndarray:
+        """The same replay with every result kept; returns the tickets (read each result
+        with result(), then release() it)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        arr = np.ascontiguousarray(np.round(np.asarray(arrival_s) * 1e9), dtype=np.uint64)
+        tickets = np.zeros(len(ids), np.uint64)
+        check(self.L.rsaprng_server_replay_keep(self.h, len(ids), _u32p(ids), _u64p(counts),
+                                                _u64p(arr), int(timeout_s * 1e9),
+                                                _u64p(tickets)), "server_replay_keep")
+        return tickets
 
     def close(self):
         if self.h:

@@ -23,6 +23,7 @@ pvp = ctypes.POINTER(ctypes.c_void_p)
 OK = 0
 MODEXP_AUTO, MODEXP_CRT32, MODEXP_MONT64 = 0, 1, 2
 DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_RECIP = 0, 1, 2, 3, 4
+LOOKBACK_AUTO, LOOKBACK_OFF = 0, 1
 E_SMALLEST, E_UNIFORM, E_AT_LEAST = 0, 1, 2
 HIST_HIGH, HIST_LOW = 0, 1
 ROUND_DEFAULT, ROUND_PAPER, ROUND_EXACT = 0, 1, 2
@@ -42,20 +43,23 @@ class Config(ctypes.Structure):
     _fields_ = [("struct_size", u32), ("modexp", i32), ("divide", i32),
                 ("threads_per_block", i32), ("numbers_per_thread", i32), ("blocks_per_sm", i32),
                 ("chunk", u64), ("require_safe", i32), ("rounding", i32),
-                ("reserved", i32 * 6)]
+                ("lookback", i32), ("spin_limit", i32), ("test_flags", i32),
+                ("reserved", i32 * 3)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("submitted", u64), ("admitted", u64), ("completed", u64), ("rejected", u64),
                 ("cancelled", u64), ("queued_now", u64), ("inflight_now", u64),
                 ("numbers_done", u64), ("p50_ms", dbl), ("p99_ms", dbl), ("mean_ms", dbl),
-                ("max_ms", dbl), ("busy_s", dbl), ("wall_s", dbl), ("iterations", u64)]
+                ("max_ms", dbl), ("busy_s", dbl), ("wall_s", dbl), ("iterations", u64),
+                ("max_inflight_iterations", u64), ("overlapped_iterations", u64)]
 
 
 # name: (restype, argtypes) for every symbol declared in include/rsaprng.h
 SIGNATURES = {
     "rsaprng_ctx_create": (i32, [pvp, i32, u64, ctypes.POINTER(Config)]),
     "rsaprng_ctx_destroy": (None, [vp]),
+    "rsaprng_device_status": (i32, [vp, vp]),
     "rsaprng_ctx_configure": (i32, [vp, ctypes.POINTER(Config)]),
     "rsaprng_ctx_get_config": (i32, [vp, ctypes.POINTER(Config)]),
     "rsaprng_instance_count": (u64, [vp]),
@@ -97,6 +101,7 @@ SIGNATURES = {
     "rsaprng_server_cancel": (i32, [vp, u64]),
     "rsaprng_server_stats": (i32, [vp, ctypes.POINTER(Stats)]),
     "rsaprng_server_replay": (i32, [vp, u64, pu32, pu64, pu64, u64, pdbl]),
+    "rsaprng_server_replay_keep": (i32, [vp, u64, pu32, pu64, pu64, u64, pu64]),
     "rsaprng_server_destroy": (None, [vp]),
     "rsaprng_is_prime": (i32, [u64]),
     "rsaprng_root_allowed": (i32, [u64]),

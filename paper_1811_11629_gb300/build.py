@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(BUILD, "librsaprng.so")
 SOURCES = ["kernels.cu", "consume.cu", "vector.cu", "api.cu", "plans.cu", "server.cpp",
-           "host_params.cpp", "plan_core.cpp", "noalloc.cu"]
+           "host_params.cpp", "plan_core.cpp", "noalloc.cu", "lookback.cu"]
 HEADERS = ["device_math.cuh", "kernels.cuh", "tile.cuh", "host_params.hpp", "api_internal.hpp",
            "work.hpp", "plan_core.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

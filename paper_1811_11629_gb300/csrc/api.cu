@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 static const rsaprng_config kDefaultConfig = {
     sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP, 128, 16, 0, 1ULL << 18, 0,
-    RSAPRNG_ROUND_DEFAULT, {0, 0, 0, 0, 0, 0}};
+    RSAPRNG_ROUND_DEFAULT, RSAPRNG_LOOKBACK_AUTO, 0, 0, {0, 0, 0}};
 
 static int check_config(const rsaprng_config &c)
 {
@@ -56,6 +56,8 @@ static int check_config(const rsaprng_config &c)
         return fail(RSAPRNG_ERR_ARG, "config: blocks_per_sm out of range");
     if (c.rounding < 0 || c.rounding > RSAPRNG_ROUND_EXACT)
         return fail(RSAPRNG_ERR_ARG, "config: rounding out of range");
+    if (c.lookback < 0 || c.lookback > RSAPRNG_LOOKBACK_OFF)
+        return fail(RSAPRNG_ERR_ARG, "config: lookback out of range");
     return RSAPRNG_OK;
 }
 
@@ -79,6 +81,9 @@ static rsaprng_config merged(const rsaprng_config &base, const rsaprng_config *o
     c.require_safe = over->require_safe;
     if (over->rounding)
         c.rounding = over->rounding;
+    c.lookback = over->lookback;
+    c.spin_limit = over->spin_limit;
+    c.test_flags = over->test_flags;
     return c;
 }
 
@@ -331,6 +336,8 @@ void free_devplan(DevPlan &dp)
         cudaFree(dp.d_sums);
     if (dp.h_buf)
         cudaFreeHost(dp.h_buf);
+    if (dp.d_lb)
+        cudaFree(dp.d_lb);
     dp = DevPlan{};
 }
 
@@ -511,6 +518,8 @@ void rsaprng_ctx_destroy(rsaprng_ctx *c)
         cudaFree(c->d_pow2k);
     if (c->d_out_scratch)
         cudaFree(c->d_out_scratch);
+    if (c->d_err)
+        cudaFree(c->d_err);
     delete c;
 }
 
@@ -897,6 +906,11 @@ static int generate_one(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c
         return fail(RSAPRNG_ERR_ID, "unknown id %u", id);
     if (N == 0)
         return RSAPRNG_OK;
+    cudaSetDevice(c->device);
+    bool done = false;
+    int rc1 = generate_single_launch(c, id, N, d_c, d_r, (cudaStream_t)stream, &done);
+    if (rc1 || done)
+        return rc1;
     const uint64_t tile = (uint64_t)c->cfg.threads_per_block * c->cfg.numbers_per_thread;
     const uint64_t target = (uint64_t)c->sms * 8;
     uint64_t chunk = (N + target - 1) / target;

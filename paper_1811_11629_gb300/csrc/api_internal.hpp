@@ -36,6 +36,12 @@ struct DevPlan {
     int vec_ts = 0;
     GenLaunch last{};  // shape of the most recent generation launch
     int occupancy = 0; // resident blocks per SM of that launch
+    // Single-launch calls: a 64-byte ticket word, then the per-tile status
+    // array; the ticket only grows, lb_base being its value before the next
+    // launch's first block.
+    void *d_lb = nullptr;
+    size_t cap_lb = 0;
+    uint64_t lb_base = 0;
 };
 
 constexpr int kScratchSlots = 4;
@@ -65,6 +71,8 @@ struct rsaprng_ctx {
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
     rsaprng::HostPlan hp_direct;  // host plan of the direct calls, rebuilt in place
+    uint32_t *d_err = nullptr;    // device error word (bit 0: a device-side wait gave up)
+    uint64_t lb_epoch = 0;        // tag of the latest single-launch call
 };
 
 namespace rsaprng {
@@ -90,5 +98,10 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
                 const HistArgs *hist = nullptr, bool fresh = false);
 void free_devplan(DevPlan &dp);
 int scratch_slot(rsaprng_ctx *c, ScratchSlot **out);
+// One instance's N outputs in one launch with a decoupled look-back, when the
+// configuration and N allow it (*done = true); otherwise nothing is launched
+// and the caller takes the chunked path.
+int generate_single_launch(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c,
+                           double *d_r, cudaStream_t st, bool *done);
 
 }  // namespace rsaprng

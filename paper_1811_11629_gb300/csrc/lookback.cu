@@ -1,0 +1,402 @@
+// Single-launch generation of one stream (the plain call of Sec. V's
+// Algorithm over one instance) with a decoupled look-back for the message
+// offsets.
+//
+// Sec. IV: the message before output k is m_0 plus the sum of the skips
+// s_1..s_k (mod n), and that sum has no cheap closed form, while the skips
+// themselves jump exactly (s_k = s_0 a^k mod Q). Here block b of the launch
+// owns tile b of the stream (outputs bS+1 .. bS+S). It jumps to its first
+// skip, sums its tile's skips (the tile aggregate) and publishes the
+// aggregate; its first warp then walks back over the tiles before it,
+// adding their aggregates until it meets a tile that has published its
+// inclusive prefix (Merrill & Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", 2016). The block publishes its own inclusive
+// prefix at once and goes on to the messages, the encryption, the division
+// and the stores of its tile.
+//
+// Waiting. A block waits only on tiles with a smaller logical index; logical
+// indices are handed out by an atomic ticket in the order blocks start, so
+// every tile a block waits on belongs to a block that has started, and every
+// started block publishes its aggregate before it waits on anything. Each
+// wait is still bounded: after spin_limit empty polls the block raises the
+// context's device error flag and returns without writing its tile (the
+// host reads the flag with rsaprng_device_status). No wait is unbounded.
+//
+// Status words carry the call's epoch (a per-context counter, never reused),
+// so the status array needs no clearing between calls.
+#include <cstdio>
+#include <mutex>
+
+#include "api_internal.hpp"
+#include "device_math.cuh"
+#include "kernels.cuh"
+#include "tile.cuh"
+
+namespace rsaprng {
+
+namespace {
+
+using dev::addmod;
+using dev::mulmodQ;
+using tile::FULL;
+using tile::sidx;
+using tile::to_unit;
+
+// Per-tile status: the tile aggregate and the inclusive prefix, each with the
+// epoch of the call that wrote it (written once per call, value before tag).
+struct LbStatus {
+    u64 agg, agg_tag;
+    u64 incl, incl_tag;
+};
+static_assert(sizeof(LbStatus) == 32, "LbStatus layout");
+
+struct LbArgs {
+    u64 N;                    // outputs of the call
+    u64 epoch;                // this call's tag
+    u64 ticket_base;          // ticket value before this launch's first block
+    unsigned long long *ticket;
+    LbStatus *status;         // one per tile
+    uint32_t *err;            // context device error word
+    uint32_t inst;
+    uint32_t ntiles;
+    uint32_t spin_limit;      // empty polls before a wait gives up
+    uint32_t inject;          // bit 0: tile 0 publishes nothing (tests of the error path)
+};
+
+__device__ __forceinline__ u64 ld_acquire(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ u64 ld_relaxed(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(u64 *p, u64 v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release(u64 *p, u64 v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Run by one whole warp for tile b > 0: the sum (mod n) of the skips of all
+// tiles before b. Lane l looks at tile top - l of the current window; the
+// window moves back 32 tiles until some tile in it has its inclusive prefix.
+// Returns false when a poll round finds a tile still empty after spin_limit
+// empty rounds (the wait gave up).
+__device__ __forceinline__ bool lookback(const LbStatus *st, uint32_t b, u64 epoch, u64 n,
+                                         uint32_t spin_limit, u64 &excl)
+{
+    const int lane = threadIdx.x & 31;
+    u64 acc = 0;
+    long long top = (long long)b - 1;
+    uint32_t empty_rounds = 0;
+    for (;;) {
+        const long long idx = top - lane;
+        u64 v = 0;
+        int kind = idx < 0 ? 2 : 0;  // 2: inclusive prefix, 1: aggregate, 0: nothing yet
+        for (;;) {
+            if (kind == 0) {
+                if (ld_acquire(&st[idx].incl_tag) == epoch) {
+                    v = ld_relaxed(&st[idx].incl);
+                    kind = 2;
+                } else if (ld_acquire(&st[idx].agg_tag) == epoch) {
+                    v = ld_relaxed(&st[idx].agg);
+                    kind = 1;
+                }
+            }
+            if (__all_sync(FULL, kind != 0))
+                break;
+            if (empty_rounds >= spin_limit)
+                return false;
+            empty_rounds++;
+            __nanosleep(64);
+        }
+        const unsigned pm = __ballot_sync(FULL, kind == 2);
+        const int stop = pm ? __ffs(pm) - 1 : 31;
+        u64 x = lane <= stop ? v : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+            x = addmod(x, __shfl_xor_sync(FULL, x, d), n);
+        acc = addmod(acc, x, n);
+        if (pm)
+            break;
+        top -= 32;
+    }
+    excl = acc;
+    return true;
+}
+
+template <int L, int MODEXP, int DIV>
+__global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbArgs A,
+                                                         double *__restrict__ out_r,
+                                                         u64 *__restrict__ out_c)
+{
+    extern __shared__ u64 smem[];
+    __shared__ u64 sh_scan[32];
+    __shared__ u64 sh_m0, sh_s0, sh_carry;
+    __shared__ uint32_t sh_b, sh_fail;
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
+    const int S = T * L;
+    const int slots = S + (S >> 4);
+    u64 *st_r = smem;
+    u64 *st_c = smem + (out_r ? slots : 0);
+    if (t == 0) {
+        // Logical tile in start order; the instance state is read before
+        // anything is published, so the block that writes the new state
+        // (the last tile, after it has seen every earlier tile's prefix
+        // chain) cannot overtake a read.
+        sh_b = (uint32_t)(atomicAdd(A.ticket, 1ull) - A.ticket_base);
+        sh_m0 = tab.state_m[A.inst];
+        sh_s0 = tab.state_s[A.inst];
+        sh_fail = 0;
+    }
+    __syncthreads();
+    const uint32_t b = sh_b;
+    if (b >= A.ntiles)
+        return;
+    const InstParams P = tab.params[A.inst];
+    const u64 *plin = tab.pow_lin + (size_t)P.root * kPowLinRow;
+    const u64 *p2k = tab.pow2k + (size_t)P.root * 64;
+    const u64 base = (u64)b * S;
+    const u64 left = A.N - base;
+    const int tile_n = left < (u64)S ? (int)left : S;
+    const int my0 = t * L;
+    const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0);
+
+    // The skip before the tile, s_0 a^(bS): lane l multiplies the table
+    // powers a^(2^(2l)) and a^(2^(2l+1)) for the set bits of bS, and a
+    // butterfly multiplies the lanes' factors (every warp computes it, so no
+    // barrier is needed).
+    const int b0 = 2 * lane;
+    u64 f = ((base >> b0) & 1) ? p2k[b0] : 1;
+    if ((base >> (b0 + 1)) & 1)
+        f = mulmodQ(f, p2k[b0 + 1]);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+        f = mulmodQ(f, __shfl_xor_sync(FULL, f, d));
+    const u64 s_thr = mulmodQ(mulmodQ(sh_s0, f), plin[my0]);
+
+    WorkItem W;
+    W.inst = A.inst;
+    W.flags = b + 1 == A.ntiles ? WI_WRITEBACK : 0u;
+    W.count = left;
+    W.out_off = base;
+    W.m0 = W.s0 = 0;
+    bool failed = false;
+    u64 carry = 0;
+    // The tile's block scan, then the look-back for its carry-in.
+    auto scan = [&](u64 v, u64 n, u64 &total) -> u64 {
+        const u64 pre = tile::block_exscan_mod(v, n, sh_scan, total);
+        if (t < 32) {
+            LbStatus *me = A.status + b;
+            u64 excl = 0;
+            bool ok = true;
+            if (b > 0) {
+                if (lane == 0) {
+                    st_relaxed(&me->agg, total);
+                    st_release(&me->agg_tag, A.epoch);
+                }
+                ok = lookback(A.status, b, A.epoch, n, A.spin_limit, excl);
+            }
+            if (lane == 0) {
+                if (ok && !(b == 0 && (A.inject & 1))) {
+                    st_relaxed(&me->incl, addmod(excl, total, n));
+                    st_release(&me->incl_tag, A.epoch);
+                }
+                if (!ok)
+                    atomicOr(A.err, 1u);
+                sh_carry = excl;
+                sh_fail = ok ? 0u : 1u;
+            }
+        }
+        __syncthreads();
+        failed = sh_fail != 0;
+        carry = sh_carry;
+        if (failed)
+            W.flags = 0;  // no state write-back after a wait that gave up
+        return addmod(carry, pre, n);
+    };
+    u64 c[L], total;
+    tile::tile_ciphertexts_scan<L, MODEXP>(tab, W, P, sh_m0, s_thr, left, my0, nvalid, scan, c,
+                                           total);
+    if (failed)
+        return;
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const int i = sidx(my0 + j);
+        if (out_r)
+            st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
+        if (out_c)
+            st_c[i] = c[j];
+    }
+    __syncthreads();
+    if (out_r) {
+        for (int i = t; i < tile_n; i += T)
+            out_r[base + i] = __longlong_as_double((long long)st_r[sidx(i)]);
+    }
+    if (out_c) {
+        for (int i = t; i < tile_n; i += T)
+            out_c[base + i] = st_c[sidx(i)];
+    }
+    if ((W.flags & WI_WRITEBACK) && t == 0)
+        tab.state_m[A.inst] = addmod(addmod(sh_m0, carry, P.n), total, P.n);
+}
+
+template <int L, int MODEXP, int DIV>
+cudaError_t launch_lb_t(int threads, const DeviceTables &tab, const LbArgs &A, double *out_r,
+                        u64 *out_c, cudaStream_t stream)
+{
+    const size_t smem = gen_smem_bytes(threads, L, out_r != nullptr, out_c != nullptr);
+    auto kern = k_generate_lookback<L, MODEXP, DIV>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    kern<<<A.ntiles, threads, smem, stream>>>(tab, A, out_r, out_c);
+    return cudaGetLastError();
+}
+
+// The tilings and routes with a single-launch kernel; others use the chunked
+// path. Returns cudaErrorNotSupported when there is none.
+cudaError_t launch_lookback(int L, int modexp, int divide, int threads, const DeviceTables &tab,
+                            const LbArgs &A, double *out_r, u64 *out_c, cudaStream_t stream)
+{
+#define RSAPRNG_LB(LL, MM, DD)                                                          \
+    if (L == LL && modexp == MM && divide == DD)                                        \
+        return launch_lb_t<LL, MM, DD>(threads, tab, A, out_r, out_c, stream);
+    RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_HYBRID)
+    RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_FP64)
+    RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_EXACT)
+    RSAPRNG_LB(8, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_LB(8, MODEXP_MONT64, DIVIDE_RECIP)
+    RSAPRNG_LB(8, MODEXP_MONT64, DIVIDE_INT)
+#undef RSAPRNG_LB
+    return cudaErrorNotSupported;
+}
+
+
+// Tiles of one single-launch call at most (the status array of a scratch
+// slot holds this many); longer draws take the chunked path.
+constexpr uint64_t kLbMaxTiles = 4096;
+// Empty poll rounds before a wait gives up when the configuration leaves the
+// limit at zero (about a second with the 64 ns pause between rounds).
+constexpr uint32_t kLbDefaultSpin = 1u << 23;
+
+int lookback_error_word(rsaprng_ctx *c, uint32_t **out)
+{
+    if (!c->d_err) {
+        cudaError_t e = cudaMalloc(&c->d_err, sizeof(uint32_t));
+        if (e != cudaSuccess)
+            return cuda_fail(e, "device error word");
+        if ((e = cudaMemset(c->d_err, 0, sizeof(uint32_t))) != cudaSuccess)
+            return cuda_fail(e, "device error word");
+    }
+    *out = c->d_err;
+    return RSAPRNG_OK;
+}
+
+}  // namespace
+
+int generate_single_launch(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *d_c,
+                           double *d_r, cudaStream_t st, bool *done)
+{
+    *done = false;
+    const rsaprng_config &cfg = c->cfg;
+    if (cfg.lookback == RSAPRNG_LOOKBACK_OFF)
+        return RSAPRNG_OK;
+    const GenLaunch g = ctx_launch(c, cfg, 1, d_r != nullptr, d_c != nullptr);
+    const uint64_t S = (uint64_t)g.threads * g.L;
+    const uint64_t ntiles = (N + S - 1) / S;
+    if (ntiles > kLbMaxTiles)
+        return RSAPRNG_OK;
+    if (g.modexp == MODEXP_MONT64 && c->h_params[id].e != c->h_params[id].eq)
+        return fail(RSAPRNG_ERR_ARG, "instance %u has CRT exponents: the 64-bit route cannot "
+                                     "run it", id);
+    uint32_t *err = nullptr;
+    int rc = lookback_error_word(c, &err);
+    if (rc)
+        return rc;
+    ScratchSlot *slot;
+    if ((rc = scratch_slot(c, &slot)) != RSAPRNG_OK)
+        return rc;
+    DevPlan &dp = slot->plan;
+    const size_t need = 64 + kLbMaxTiles * sizeof(LbStatus);
+    if (dp.cap_lb < need) {
+        if (dp.d_lb)
+            cudaFree(dp.d_lb);
+        dp.d_lb = nullptr;
+        dp.cap_lb = 0;
+        cudaError_t e = cudaMalloc(&dp.d_lb, need);
+        if (e != cudaSuccess)
+            return fail(RSAPRNG_ERR_OOM, "single-launch status (%zu bytes)", need);
+        // zero tags match no epoch (epochs start at 1); the ticket starts at 0
+        if ((e = cudaMemsetAsync(dp.d_lb, 0, need, st)) != cudaSuccess)
+            return cuda_fail(e, "single-launch status");
+        dp.cap_lb = need;
+        dp.lb_base = 0;
+    }
+    LbArgs A;
+    A.N = N;
+    A.epoch = ++c->lb_epoch;
+    A.ticket_base = dp.lb_base;
+    A.ticket = (unsigned long long *)dp.d_lb;
+    A.status = (LbStatus *)((char *)dp.d_lb + 64);
+    A.err = err;
+    A.inst = id;
+    A.ntiles = (uint32_t)ntiles;
+    A.spin_limit = cfg.spin_limit > 0 ? (uint32_t)cfg.spin_limit
+                   : cfg.spin_limit < 0 ? 0u
+                                        : kLbDefaultSpin;
+    A.inject = (uint32_t)cfg.test_flags;
+    cudaError_t e = launch_lookback(g.L, g.modexp, g.divide, g.threads, ctx_tables(c), A, d_r,
+                                    d_c, st);
+    if (e == cudaErrorNotSupported) {
+        (void)cudaGetLastError();
+        return RSAPRNG_OK;  // no single-launch kernel for this tiling: the chunked path
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "single-launch generation");
+    dp.lb_base += ntiles;
+    cudaEventRecord(slot->done, st);
+    slot->used = true;
+    c->launches += 1;
+    *done = true;
+    return RSAPRNG_OK;
+}
+
+}  // namespace rsaprng
+
+extern "C" int rsaprng_device_status(rsaprng_ctx *c, void *stream)
+{
+    using namespace rsaprng;
+    if (!c)
+        return fail(RSAPRNG_ERR_ARG, "null ctx");
+    if (!c->d_err)
+        return RSAPRNG_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t flag = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&flag, c->d_err, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "device status");
+    if (!flag)
+        return RSAPRNG_OK;
+    if ((e = cudaMemset(c->d_err, 0, sizeof flag)) != cudaSuccess)
+        return cuda_fail(e, "device status");
+    return fail(RSAPRNG_ERR_DEVICE_FLAG, "a device-side wait gave up (flags 0x%x)", flag);
+}
