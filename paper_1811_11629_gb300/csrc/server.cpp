@@ -105,6 +105,7 @@ struct Piece {
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr;  // recorded before the iteration's upload
     cudaEvent_t done = nullptr;
     DevPlan plan;
     bool busy = false;
@@ -139,6 +140,11 @@ struct rsaprng_server {
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, cancelled = 0;
     uint64_t numbers_done = 0, iterations = 0;
+    uint64_t max_inflight = 0, overlapped = 0;
+    // Device intervals (ms after t_ref) of the most recently retired
+    // iterations, to count the iterations that ran beside another one.
+    cudaEvent_t t_ref = nullptr;
+    std::deque<std::pair<float, float>> recent;
     std::vector<double> lat_ms;
     double t_first = 0, t_last = 0, busy_s = 0;
     int error = RSAPRNG_OK;
@@ -197,7 +203,21 @@ bool retire(rsaprng_server *S, bool block_oldest)
             S->error_detail = cudaGetErrorString(q);
         }
         const double t = now_s();
+        float d0 = 0, d1 = 0;
+        const bool timed = cudaEventElapsedTime(&d0, S->t_ref, sl.start) == cudaSuccess &&
+                           cudaEventElapsedTime(&d1, S->t_ref, sl.done) == cudaSuccess;
         std::lock_guard<std::mutex> lk(S->mu);
+        if (timed) {
+            // Retired in any order: compare with every recent interval.
+            for (const auto &iv : S->recent)
+                if (d0 < iv.second && iv.first < d1) {
+                    S->overlapped++;
+                    break;
+                }
+            S->recent.emplace_back(d0, d1);
+            if (S->recent.size() > 64)
+                S->recent.pop_front();
+        }
         S->busy_s += t - sl.t_launch;
         for (rsaprng_id id : sl.insts)
             if (S->busy[id] == sl.iter)
@@ -289,6 +309,7 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     chunk = std::max<uint64_t>(tile, (chunk + tile - 1) / tile * tile);
     chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(S->ctx->cfg.chunk, tile));
     HostPlan hp;
+    cudaEventRecord(sl.start, sl.stream);
     int rc = build_plan(S->ctx, S->ctx->cfg, ids.size(), ids.data(), counts.data(), offs.data(),
                         chunk, hp);
     if (rc == RSAPRNG_OK)
@@ -299,7 +320,11 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     cudaEventRecord(sl.done, sl.stream);
     sl.t_launch = now_s();
     sl.busy = true;
+    uint64_t in_flight = 0;
+    for (auto &o : S->slots)
+        in_flight += o.busy ? 1 : 0;
     std::lock_guard<std::mutex> lk(S->mu);
+    S->max_inflight = std::max(S->max_inflight, in_flight);
     S->iterations++;
     if (rc != RSAPRNG_OK) {
         S->error = rc;
@@ -366,8 +391,12 @@ int rsaprng_server_create(rsaprng_ctx *c, uint64_t out_budget_bytes, int nstream
     S->slots.resize(nstreams);
     for (auto &sl : S->slots) {
         cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        cudaEventCreate(&sl.start);
+        cudaEventCreate(&sl.done);
     }
+    cudaEventCreate(&S->t_ref);
+    cudaEventRecord(S->t_ref, S->slots[0].stream);
+    cudaEventSynchronize(S->t_ref);
     S->busy.assign(c->capacity, 0);
     S->stamp.assign(c->capacity, 0);
     S->t_first = now_s();
@@ -541,6 +570,8 @@ int rsaprng_server_stats(rsaprng_server *S, rsaprng_stats *out)
     out->inflight_now = infl;
     out->numbers_done = S->numbers_done;
     out->iterations = S->iterations;
+    out->max_inflight_iterations = S->max_inflight;
+    out->overlapped_iterations = S->overlapped;
     out->busy_s = S->busy_s;
     out->wall_s = (S->t_last > S->t_first ? S->t_last : now_s()) - S->t_first;
     if (!S->lat_ms.empty()) {
@@ -565,9 +596,9 @@ int rsaprng_server_stats(rsaprng_server *S, rsaprng_stats *out)
 // arrival_ns[i] (nanoseconds after the call starts) with its outputs released
 // as soon as they complete. Returns when every request has completed (or
 // timeout_ns passes). Latencies (ms) go to lat_ms_out[i] when non-NULL.
-int rsaprng_server_replay(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
-                          const uint64_t *counts, const uint64_t *arrival_ns, uint64_t timeout_ns,
-                          double *lat_ms_out)
+static int replay_impl(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
+                       const uint64_t *counts, const uint64_t *arrival_ns, uint64_t timeout_ns,
+                       double *lat_ms_out, uint64_t *tickets_out)
 {
     if (!S || (n && (!ids || !counts || !arrival_ns)))
         return fail(RSAPRNG_ERR_ARG, "server_replay: null argument");
@@ -578,6 +609,8 @@ int rsaprng_server_replay(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
         S->submitted = S->admitted = S->completed = S->rejected = 0;
         S->iterations = 0;
         S->busy_s = 0;
+        S->max_inflight = S->overlapped = 0;
+        S->recent.clear();
     }
     std::vector<uint64_t> tickets(n, 0);
     const auto t0 = clk::now();
@@ -593,9 +626,11 @@ int rsaprng_server_replay(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
                 std::this_thread::sleep_for(left - std::chrono::microseconds(100));
         }
         const double ts = std::chrono::duration<double>(due.time_since_epoch()).count();
-        int rc = submit_impl(S, ids[i], counts[i], &tickets[i], true, ts);
+        int rc = submit_impl(S, ids[i], counts[i], &tickets[i], tickets_out == nullptr, ts);
         if (rc)
             return rc;
+        if (tickets_out)
+            tickets_out[i] = tickets[i];
     }
     std::unique_lock<std::mutex> lk(S->mu);
     const auto deadline = clk::now() + std::chrono::nanoseconds(timeout_ns);
@@ -610,6 +645,22 @@ int rsaprng_server_replay(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
         for (uint64_t i = 0; i < n && i < S->lat_ms.size(); i++)
             lat_ms_out[i] = S->lat_ms[i];
     return RSAPRNG_OK;
+}
+
+int rsaprng_server_replay(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
+                          const uint64_t *counts, const uint64_t *arrival_ns, uint64_t timeout_ns,
+                          double *lat_ms_out)
+{
+    return replay_impl(S, n, ids, counts, arrival_ns, timeout_ns, lat_ms_out, nullptr);
+}
+
+int rsaprng_server_replay_keep(rsaprng_server *S, uint64_t n, const rsaprng_id *ids,
+                               const uint64_t *counts, const uint64_t *arrival_ns,
+                               uint64_t timeout_ns, uint64_t *tickets_out)
+{
+    if (!tickets_out)
+        return fail(RSAPRNG_ERR_ARG, "server_replay_keep: null tickets");
+    return replay_impl(S, n, ids, counts, arrival_ns, timeout_ns, nullptr, tickets_out);
 }
 
 void rsaprng_server_destroy(rsaprng_server *S)
@@ -638,9 +689,13 @@ void rsaprng_server_destroy(rsaprng_server *S)
         free_devplan(sl.plan);
         if (sl.done)
             cudaEventDestroy(sl.done);
+        if (sl.start)
+            cudaEventDestroy(sl.start);
         if (sl.stream)
             cudaStreamDestroy(sl.stream);
     }
+    if (S->t_ref)
+        cudaEventDestroy(S->t_ref);
     if (S->d_arena)
         cudaFree(S->d_arena);
     delete S->arena;

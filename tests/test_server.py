@@ -156,3 +156,50 @@ def test_server_serves_every_mode(O):
         c, _, _, _ = O.generate(p, q, e, m0, s0, len(seq), a=a, eq=eqq)
         want = O.unit_exact_many(c, p * q)
         assert (seq.view(np.uint64) == want.view(np.uint64)).all()
+
+
+def test_continuous_batching_poisson_arrivals(O):
+    """Continuous batching, not a queue: requests arrive (Poisson, paced by the native
+    replay) while earlier ones run; iterations overlap on the device (their event
+    intervals on different streams overlap); and every request's outputs equal its
+    instance's stream at the request's position, replayed alone by the oracle."""
+    ctx = R.Context(128)
+    ids, par = _instances(ctx, O, master=40, k=64, rule=R.E_UNIFORM, lo=3, hi=257)
+    nreq = 1500
+    pick = ids[workload.uniform_indices(41, nreq, len(ids))]
+    cnt = workload.loguniform_counts(42, nreq, lo=1 << 10, hi=1 << 19)
+    arrivals = workload.poisson_arrivals(43, nreq, rate_per_s=200_000.0)
+    total = int(cnt.sum())
+    srv = R.Server(ctx, out_budget_bytes=8 * total + (1 << 20), nstreams=3)
+    tickets = srv.replay_keep(pick, cnt, arrivals, timeout_s=300)
+    st = srv.stats()
+    assert st["completed"] == nreq
+    assert st["max_inflight_iterations"] >= 2
+    assert st["overlapped_iterations"] >= 1
+    assert st["iterations"] > 1
+    got = [srv.result(int(t)).cpu().numpy() for t in tickets]
+    for t in tickets:
+        srv.release(int(t))
+    srv.close()
+    # the oracle: each instance alone, its requests concatenated in arrival order
+    first = int(ids[0])
+    per = {}
+    for i, c in zip(pick, cnt):
+        per.setdefault(int(i), []).append(int(c))
+    keys = sorted(per)
+    p = np.array([par[i - first][0] for i in keys], np.uint64)
+    q = np.array([par[i - first][1] for i in keys], np.uint64)
+    e = np.array([par[i - first][2] for i in keys], np.uint64)
+    a = np.full(len(keys), R.DEFAULT_ROOT, np.uint64)
+    m = np.array([par[i - first][3] % (par[i - first][0] * par[i - first][1]) for i in keys],
+                 np.uint64)
+    s = np.ones(len(keys), np.uint64)
+    counts = np.array([sum(per[i]) for i in keys], np.uint64)
+    _, ref = O.generate_many(p, q, e, a, m, s, counts, route=O.ROUTE_DIRECT, want_c=False)
+    start = dict(zip(keys, np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)))
+    pos = {i: 0 for i in keys}
+    for j, (i, c) in enumerate(zip(pick, cnt)):
+        i, c = int(i), int(c)
+        o = int(start[i]) + pos[i]
+        assert (got[j].view(np.uint64) == ref[o:o + c].view(np.uint64)).all(), f"request {j}"
+        pos[i] += c
