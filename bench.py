@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--parents", type=int, default=1024,
                     help="split parents of the interleaved form (small profiling runs only)")
     ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
+    ap.add_argument("--tune-cache", default="",
+                    help="tuning-cache file: loaded before the run if it exists, saved after")
     ap.add_argument("--instances", type=int, default=0,
                     help="override the instance count (small profiling runs only)")
     ap.add_argument("--count", type=int, default=0,
@@ -401,7 +403,7 @@ def form_plain(R, torch, device, pk, rank) -> dict:
 
 def form_batched(R, torch, device, pk, rank) -> dict:
     """Batched uneven: 1e5 instances, lognormal lengths (~2^32 outputs, f64), one plan in a
-    CUDA graph after autotuning on a 2000-instance sample."""
+    CUDA graph after autotuning on the whole workload (or a tuning-cache hit)."""
     cfg = workload.CONFIGS["batched_1e5_lognormal"]
     k = cfg["instances"]
     lens = workload.lognormal_lengths(cfg["master"] + 1000 * rank, k)
@@ -409,7 +411,7 @@ def form_batched(R, torch, device, pk, rank) -> dict:
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
                               cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
-    tuned = ctx.autotune(ids[:2000], lens[:2000], reps=3)
+    tuned, from_cache = ctx.autotune_cached(ids, lens, reps=1)
     plan = ctx.plan(ids, lens)
     total = int(lens.sum())
     out = torch.empty(total, dtype=torch.float64, device="cuda")
@@ -429,7 +431,10 @@ def form_batched(R, torch, device, pk, rank) -> dict:
     res = {"value": round(total / dt / 1e9, 3), "unit": UNIT, "ms_per_replay": round(dt * 1e3, 3),
            "numbers": total, "launches_per_replay": plan.info()["launches"],
            "chunks": plan.info()["chunks"],
-           "tuned": {x: tuned[x] for x in TUNED_KEYS if x in tuned}}
+           "tuned": {x: tuned[x] for x in TUNED_KEYS if x in tuned},
+           "tuned_from_cache": from_cache,
+           "tuning": "rsaprng_autotune_cached on the whole workload (routes, tilings, "
+                     "unroll, streams per block, blocks per SM, chunk cap)"}
     res.update(bounds(pk, total, _slots(es, lens), dt, ctx.config()["divide"], 8))
     plan.close()
     del out
@@ -575,7 +580,7 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     pick = first + workload.uniform_indices(61, nreq, k)
     cnt = workload.loguniform_counts(62, nreq, lo=16, hi=1 << 24)
     # tune the tiling on a sample of the request mix (the instance states are restored)
-    tuned = ctx.autotune(pick[:512], np.minimum(cnt[:512], 1 << 20), reps=3)
+    tuned, _ = ctx.autotune_cached(pick[:512], np.minimum(cnt[:512], 1 << 20), reps=3)
     srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
     mean_cnt = float(cnt.mean())
     # capacity: all requests at once (arrival 0), the server batching freely
@@ -638,6 +643,8 @@ def run_ours(args) -> int:
     counts = np.full(k, n, np.uint64)
     es = [ctx.params(int(i))[2] for i in ids]
     pk = measure_peaks(ctx, torch, dist.local_rank)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        R._lib.check(ctx.L.rsaprng_autotune_cache_load(args.tune_cache.encode()), "cache load")
     tuned = None
     if args.tune:
         tuned = ctx.autotune(ids, counts, reps=1)
@@ -767,6 +774,8 @@ def run_ours(args) -> int:
         result["forms"] = {name: fn() for name, key, fn in runs if key in want}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)
+    if args.tune_cache:
+        R._lib.check(ctx.L.rsaprng_autotune_cache_save(args.tune_cache.encode()), "cache save")
     if dist.rank == 0:
         print(json.dumps(result), flush=True)
     plan.close()

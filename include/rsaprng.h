@@ -129,7 +129,16 @@ typedef struct {
                                    single-launch call publishes no prefix, so every
                                    later tile's wait runs out (tests of the device
                                    error path; no GPU fault is involved) */
-    int32_t reserved[3];
+    int32_t streams_per_block;  /* generation plans: 1 = one stream per block; 2, 4, 8
+                                   or 16 = that many streams side by side in a block,
+                                   threads_per_block / streams_per_block threads each
+                                   (at least a warp), pieces grouped by length */
+    int32_t unroll;             /* independent exponentiation chains a thread runs at
+                                   once: 0 = all numbers_per_thread; a smaller power of
+                                   two runs them in passes of that many (128 x 16 CRT
+                                   tiles with 8, 8-per-thread CRT reciprocal tiles with
+                                   4; other tilings run all at once) */
+    int32_t reserved[1];
 } rsaprng_config;
 
 enum {
@@ -343,12 +352,34 @@ void rsaprng_plan_destroy(rsaprng_plan *plan);
 
 /* --------------------------------------------------------------- tuning */
 
-/* Times the candidate tilings and routes on a plan built from the given
- * requests (outputs go to scratch buffers the call allocates and frees) and
- * stores the fastest in the context's config. Every candidate gives
- * bit-identical outputs. */
+/* Times candidate configurations on a plan built from the given requests
+ * (outputs go to scratch buffers the call allocates and frees; instance
+ * states are restored after every trial) and stores the fastest in the
+ * context's config and in the process's tuning cache. Stages, each starting
+ * from the best so far: modexp and division routes; threads per block and
+ * numbers per thread; unroll (chains in passes of half the numbers, where a
+ * variant exists); streams per block (2, 4); resident blocks per SM (one or
+ * two below the occupancy limit); the chunk cap of long streams. Every
+ * candidate gives bit-identical outputs. `reps` timed launches per trial. */
 int rsaprng_autotune(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
                      const uint64_t *counts, int reps, rsaprng_config *chosen);
+/* As rsaprng_autotune, but first looks the workload up in the tuning cache,
+ * keyed by device (compute capability, SM count), workload signature
+ * (log2 buckets of the request count, the mean and the longest request; the
+ * rounding reading) and exponent class (mean Montgomery products per
+ * output, in steps of two). On a hit the cached knobs are applied at once
+ * and *from_cache (may be NULL) is 1; otherwise it tunes. */
+int rsaprng_autotune_cached(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
+                            const uint64_t *counts, int reps, rsaprng_config *chosen,
+                            int *from_cache);
+/* The tuning cache: entries held, clear, and a text file of one line per
+ * entry (key, then name=value knobs) to keep tuned choices across
+ * processes. Load adds to (and overrides) the entries held; RSAPRNG_ERR_ARG
+ * for an unreadable file or a malformed line (nothing is added then). */
+uint64_t rsaprng_autotune_cache_size(void);
+void rsaprng_autotune_cache_clear(void);
+int rsaprng_autotune_cache_save(const char *path);
+int rsaprng_autotune_cache_load(const char *path);
 
 /* -------------------------------------------------------------- serving */
 

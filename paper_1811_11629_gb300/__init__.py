@@ -298,6 +298,17 @@ class Context:
                                       ctypes.byref(c)), "autotune")
         return {f: getattr(c, f) for f, _ in Config._fields_ if f not in ("reserved",)}
 
+    def autotune_cached(self, ids, counts, reps: int = 2):
+        """The tuning-cache lookup, tuning on a miss; returns (config dict, from_cache)."""
+        ids, counts, _ = self._req(ids, counts, None)
+        c = Config()
+        hit = ctypes.c_int32()
+        check(self.L.rsaprng_autotune_cached(self.h, len(ids), _u32p(ids), _u64p(counts), reps,
+                                             ctypes.byref(c), ctypes.byref(hit)),
+              "autotune_cached")
+        return {f: getattr(c, f) for f, _ in Config._fields_ if f not in ("reserved",)}, \
+            bool(hit.value)
+
     def microbench(self, kind: int, nbytes: int = 0) -> float:
         r = ctypes.c_double()
         check(self.L.rsaprng_microbench(self.h, kind, nbytes, ctypes.byref(r)), "microbench")

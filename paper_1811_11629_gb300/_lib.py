@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
                 ("threads_per_block", i32), ("numbers_per_thread", i32), ("blocks_per_sm", i32),
                 ("chunk", u64), ("require_safe", i32), ("rounding", i32),
                 ("lookback", i32), ("spin_limit", i32), ("test_flags", i32),
-                ("reserved", i32 * 3)]
+                ("streams_per_block", i32), ("unroll", i32), ("reserved", i32 * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -91,6 +91,12 @@ SIGNATURES = {
                                  ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     "rsaprng_plan_destroy": (None, [vp]),
     "rsaprng_autotune": (i32, [vp, u64, pu32, pu64, i32, ctypes.POINTER(Config)]),
+    "rsaprng_autotune_cached": (i32, [vp, u64, pu32, pu64, i32, ctypes.POINTER(Config),
+                                      ctypes.POINTER(i32)]),
+    "rsaprng_autotune_cache_size": (u64, []),
+    "rsaprng_autotune_cache_clear": (None, []),
+    "rsaprng_autotune_cache_save": (i32, [ctypes.c_char_p]),
+    "rsaprng_autotune_cache_load": (i32, [ctypes.c_char_p]),
     "rsaprng_server_create": (i32, [vp, u64, i32, pvp]),
     "rsaprng_server_submit": (i32, [vp, u32, u64, pu64]),
     "rsaprng_server_poll": (i32, [vp, u64, ctypes.POINTER(i32)]),

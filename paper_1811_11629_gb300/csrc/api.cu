@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 static const rsaprng_config kDefaultConfig = {
     sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP, 128, 16, 0, 1ULL << 18, 0,
-    RSAPRNG_ROUND_DEFAULT, RSAPRNG_LOOKBACK_AUTO, 0, 0, {0, 0, 0}};
+    RSAPRNG_ROUND_DEFAULT, RSAPRNG_LOOKBACK_AUTO, 0, 0, 1, 0, {0}};
 
 static int check_config(const rsaprng_config &c)
 {
@@ -58,6 +58,14 @@ static int check_config(const rsaprng_config &c)
         return fail(RSAPRNG_ERR_ARG, "config: rounding out of range");
     if (c.lookback < 0 || c.lookback > RSAPRNG_LOOKBACK_OFF)
         return fail(RSAPRNG_ERR_ARG, "config: lookback out of range");
+    if (c.streams_per_block < 0 || c.streams_per_block > 16 ||
+        (c.streams_per_block & (c.streams_per_block - 1)))
+        return fail(RSAPRNG_ERR_ARG, "config: streams_per_block must be 0, 1, 2, 4, 8 or 16");
+    if (c.threads_per_block && c.streams_per_block > 1 &&
+        c.threads_per_block / c.streams_per_block < 32)
+        return fail(RSAPRNG_ERR_ARG, "config: streams_per_block leaves a stream less than a warp");
+    if (c.unroll < 0 || c.unroll > 16 || (c.unroll & (c.unroll - 1)))
+        return fail(RSAPRNG_ERR_ARG, "config: unroll must be 0, 1, 2, 4, 8 or 16");
     return RSAPRNG_OK;
 }
 
@@ -81,6 +89,10 @@ static rsaprng_config merged(const rsaprng_config &base, const rsaprng_config *o
     c.require_safe = over->require_safe;
     if (over->rounding)
         c.rounding = over->rounding;
+    if (over->streams_per_block)
+        c.streams_per_block = over->streams_per_block;
+    if (over->unroll)
+        c.unroll = over->unroll;
     c.lookback = over->lookback;
     c.spin_limit = over->spin_limit;
     c.test_flags = over->test_flags;
@@ -113,12 +125,16 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
                : cfg.divide == RSAPRNG_DIVIDE_HYBRID ? DIVIDE_HYBRID
                : cfg.divide == RSAPRNG_DIVIDE_RECIP  ? DIVIDE_RECIP
                                                      : DIVIDE_INT;
+    g.unroll = cfg.unroll > 0 && cfg.unroll < g.L ? cfg.unroll : 0;
+    if (g.unroll && !gen_has_unroll(g.L, g.modexp, g.divide, g.unroll))
+        g.unroll = 0;  // no pass-limited variant: all chains at once
     const size_t smem = gen_smem_bytes(g.threads, g.L, want_r, want_c);
     // Occupancy queries cost microseconds; cache them per kernel and smem size.
     const int ti = g.threads == 64 ? 0 : (g.threads == 128 ? 1 : (g.threads == 256 ? 2 : 3));
     const int li = g.L == 2 ? 0 : (g.L == 4 ? 1 : (g.L == 8 ? 2 : 3));
-    int &cached = c->occ_cache[ti][li][g.modexp - 1][g.divide - 1];
-    size_t &cached_smem = c->occ_smem[ti][li][g.modexp - 1][g.divide - 1];
+    const int ui = g.unroll ? 1 : 0;
+    int &cached = c->occ_cache[ti][li][g.modexp - 1][g.divide - 1][ui];
+    size_t &cached_smem = c->occ_smem[ti][li][g.modexp - 1][g.divide - 1][ui];
     int occ;
     if (cached > 0 && cached_smem == smem) {
         occ = cached;
@@ -149,15 +165,19 @@ static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t 
 
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
-               uint64_t tuple, uint64_t stride)
+               uint64_t tuple, uint64_t stride, bool allow_pack)
 {
     // The pieces are sized for the resident blocks and the tiles of the
-    // kernel that runs the plan.
-    const GenLaunch full = stride > 1 ? vec_launch(c, cfg, ~0ULL, true, false)
-                                      : ctx_launch(c, cfg, ~0ULL, true, false);
+    // kernel that runs the plan: the vector kernel for the interleaved order
+    // and for several streams per block, else the generation kernel.
+    const uint64_t pack = allow_pack && stride == 1 && tuple == 1 && cfg.streams_per_block > 1
+                              ? (uint64_t)cfg.streams_per_block
+                              : 1;
+    const GenLaunch full = (stride > 1 || pack > 1) ? vec_launch(c, cfg, ~0ULL, true, false)
+                                                    : ctx_launch(c, cfg, ~0ULL, true, false);
     const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid};
     return build_plan_core(c->h_params.data(), c->count, cfg.modexp, geo, nreq, ids, counts,
-                           offsets, chunk, hp, tuple, stride);
+                           offsets, chunk, hp, tuple, stride, pack);
 }
 
 static int grow(void **p, size_t *cap, size_t need)
@@ -284,7 +304,7 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
     cudaError_t e;
-    const bool vec = !hist && dp.stride > 1 && dp.nvecs;
+    const bool vec = !hist && dp.nvecs;  // interleaved order, or packed streams
     GenLaunch g{};
     if (dp.nitems) {
         g = hist  ? hist_launch(c, cfg, dp.nitems)
@@ -775,7 +795,7 @@ int rsaprng_generate_batch(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
     cudaSetDevice(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     HostPlan &hp = c->hp_direct;
-    int rc = build_plan(c, c->cfg, nreq, ids, counts, out_offsets, c->cfg.chunk, hp);
+    int rc = build_plan(c, c->cfg, nreq, ids, counts, out_offsets, c->cfg.chunk, hp, 1, 1, true);
     if (rc)
         return rc;
     if (hp.items.empty())

@@ -66,8 +66,9 @@ struct rsaprng_ctx {
     int next_slot = 0;
     uint64_t launches = 0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device bytes moved by the library
-    int occ_cache[4][4][2][5];  // blocks/SM by (threads 64/128/256/512, L index, modexp, divide)
-    size_t occ_smem[4][4][2][5];
+    // blocks/SM by (threads 64/128/256/512, L index, modexp, divide, passes)
+    int occ_cache[4][4][2][5][2];
+    size_t occ_smem[4][4][2][5][2];
     void *d_out_scratch = nullptr;  // device staging for host-buffer generation
     size_t cap_out_scratch = 0;
     rsaprng::HostPlan hp_direct;  // host plan of the direct calls, rebuilt in place
@@ -84,9 +85,11 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
 // Pieces of a stream are whole tiles; with tuple > 1 they are also whole
 // multiples of tuple outputs (the histogram consumer's D-tuples). Output k of
 // request i goes to element offsets[i] + k stride.
+// allow_pack: generation plans may put several streams in a block
+// (cfg.streams_per_block); the histogram consumer's plans may not.
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
-               uint64_t tuple = 1, uint64_t stride = 1);
+               uint64_t tuple = 1, uint64_t stride = 1, bool allow_pack = false);
 int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t stream);
 // Launches the pre-pass and the generation kernel, or the histogram
 // consumer instead of the generation kernel when hist is given. fresh: the

@@ -52,7 +52,8 @@ constexpr bool tuned_tile()
     return L == 16 && MODEXP == MODEXP_CRT32;
 }
 
-template <int L, int MODEXP, int DIV, int TB>
+// U < L: the encryption runs in passes of U chains (the unroll knob).
+template <int L, int MODEXP, int DIV, int TB, int U = L>
 __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
                                                   uint32_t nitems, uint32_t *ticket,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
             const int my0 = t * L;
             const int nvalid = tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0);
             u64 c[L], total;
-            tile::tile_ciphertexts<L, MODEXP>(tab, W, P, m, s_thr, left, my0, nvalid, sh_scan, c,
+            tile::tile_ciphertexts<L, MODEXP, U>(tab, W, P, m, s_thr, left, my0, nvalid, sh_scan, c,
                                               total);
 #pragma unroll
             for (int j = 0; j < L; j++) {
@@ -272,22 +273,22 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
     }
 }
 
-template <int L, int MODEXP, int DIV>
+template <int L, int MODEXP, int DIV, int U = L>
 auto gen_kernel(int threads)
 {
     if constexpr (tuned_tile<L, MODEXP>())
         if (threads == kTunedThreads)
-            return k_generate<L, MODEXP, DIV, kTunedThreads>;
-    return k_generate<L, MODEXP, DIV, 0>;
+            return k_generate<L, MODEXP, DIV, kTunedThreads, U>;
+    return k_generate<L, MODEXP, DIV, 0, U>;
 }
 
-template <int L, int MODEXP, int DIV>
+template <int L, int MODEXP, int DIV, int U = L>
 cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                          uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
                          cudaStream_t stream)
 {
     const size_t smem = gen_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = gen_kernel<L, MODEXP, DIV>(g.threads);
+    auto kern = gen_kernel<L, MODEXP, DIV, U>(g.threads);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -298,14 +299,30 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
                          g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride);
 }
 
-template <int L, int MODEXP, int DIV>
+template <int L, int MODEXP, int DIV, int U = L>
 const void *gen_kernel_ptr(int threads)
 {
-    return (const void *)gen_kernel<L, MODEXP, DIV>(threads);
+    return (const void *)gen_kernel<L, MODEXP, DIV, U>(threads);
 }
 
-const void *select_kernel(int L, int modexp, int divide, int threads)
+// The tilings with a pass-limited (unroll) variant: 16 per thread on the CRT
+// route (passes of 8) and 8 per thread with reciprocal division (passes of 4).
+#define RSAPRNG_UNROLLED(X)                      \
+    X(16, MODEXP_CRT32, DIVIDE_RECIP, 8)         \
+    X(16, MODEXP_CRT32, DIVIDE_HYBRID, 8)        \
+    X(16, MODEXP_CRT32, DIVIDE_INT, 8)           \
+    X(8, MODEXP_CRT32, DIVIDE_RECIP, 4)
+
+const void *select_kernel(int L, int modexp, int divide, int threads, int unroll)
 {
+    if (unroll > 0 && unroll < L) {
+#define RSAPRNG_SELU(LL, MM, DD, UU)                                         \
+    if (L == LL && modexp == MM && divide == DD && unroll == UU)             \
+        return gen_kernel_ptr<LL, MM, DD, UU>(threads);
+        RSAPRNG_UNROLLED(RSAPRNG_SELU)
+#undef RSAPRNG_SELU
+        return nullptr;
+    }
 #define RSAPRNG_SEL(LL, MM, DD)                                   \
     if (L == LL && modexp == MM && divide == DD)                  \
         return gen_kernel_ptr<LL, MM, DD>(threads);
@@ -517,6 +534,14 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
                             uint32_t nitems, uint32_t *ticket, double *out_r, uint64_t *out_c,
                             cudaStream_t stream)
 {
+    if (g.unroll > 0 && g.unroll < g.L) {
+#define RSAPRNG_DISPATCHU(LL, MM, DD, UU)                                                   \
+    if (g.L == LL && g.modexp == MM && g.divide == DD && g.unroll == UU)                    \
+        return launch_gen_t<LL, MM, DD, UU>(g, t, items, nitems, ticket, out_r, out_c, stream);
+        RSAPRNG_UNROLLED(RSAPRNG_DISPATCHU)
+#undef RSAPRNG_DISPATCHU
+        return cudaErrorNotSupported;  // no pass-limited kernel for this tiling
+    }
 #define RSAPRNG_DISPATCH(LL, MM, DD)                                                      \
     if (g.L == LL && g.modexp == MM && g.divide == DD)                                    \
         return launch_gen_t<LL, MM, DD>(g, t, items, nitems, ticket, out_r, out_c, stream);
@@ -559,9 +584,14 @@ cudaError_t launch_generate(const GenLaunch &g, const DeviceTables &t, const Wor
     return cudaErrorInvalidValue;
 }
 
+bool gen_has_unroll(int L, int modexp, int divide, int unroll)
+{
+    return select_kernel(L, modexp, divide, 128, unroll) != nullptr;
+}
+
 int gen_blocks_per_sm(const GenLaunch &g, size_t smem)
 {
-    const void *k = select_kernel(g.L, g.modexp, g.divide, g.threads);
+    const void *k = select_kernel(g.L, g.modexp, g.divide, g.threads, g.unroll);
     if (!k)
         return 0;
     if (smem > 48 * 1024)

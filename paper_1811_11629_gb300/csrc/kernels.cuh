@@ -42,6 +42,7 @@ struct GenLaunch {
     bool persistent; // items pulled from *ticket
     uint64_t stride; // element distance between consecutive outputs of a work item
     bool pdl = false;  // launch as a programmatic dependent of the start-state scan
+    int unroll = 0;    // 0 or >= L: all L chains at once; else passes of this many
 };
 
 // Launches kern; with pdl as a programmatic dependent of the kernel before it
@@ -110,6 +111,9 @@ cudaError_t microbench_mul(int shape, double *gops, cudaStream_t stream);
 cudaError_t microbench_fp64(int shape, double *gops, cudaStream_t stream);
 cudaError_t microbench_write(void *buf, size_t bytes, double *gbs, cudaStream_t stream);
 
+// Whether the generation kernel has a variant running its chains in passes
+// of `unroll` for this tiling and route.
+bool gen_has_unroll(int L, int modexp, int divide, int unroll);
 // Kernel attribute query for occupancy-based grid sizing.
 int gen_blocks_per_sm(const GenLaunch &g, size_t smem);
 

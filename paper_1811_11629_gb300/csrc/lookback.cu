@@ -7,8 +7,8 @@
 // themselves jump exactly (s_k = s_0 a^k mod Q). Here block b of the launch
 // owns tile b of the stream (outputs bS+1 .. bS+S). It jumps to its first
 // skip, sums its tile's skips (the tile aggregate) and publishes the
-// aggregate; its first warp then walks back over the tiles before it,
-// adding their aggregates until it meets a tile that has published its
+// aggregate; then its threads walk back over the tiles before it, many at
+// once, adding their aggregates up to the nearest tile that has published its
 // inclusive prefix (Merrill & Garland, "Single-pass Parallel Prefix Scan
 // with Decoupled Look-back", 2016). The block publishes its own inclusive
 // prefix at once and goes on to the messages, the encryption, the division
@@ -87,51 +87,62 @@ __device__ __forceinline__ void st_release(u64 *p, u64 v)
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Run by one whole warp for tile b > 0: the sum (mod n) of the skips of all
-// tiles before b. Lane l looks at tile top - l of the current window; the
-// window moves back 32 tiles until some tile in it has its inclusive prefix.
-// Returns false when a poll round finds a tile still empty after spin_limit
-// empty rounds (the wait gave up).
-__device__ __forceinline__ bool lookback(const LbStatus *st, uint32_t b, u64 epoch, u64 n,
-                                         uint32_t spin_limit, u64 &excl)
+// Run by every thread of the block for tile b > 0, after the block has
+// published its own aggregate: the sum (mod n) of the skips of all tiles
+// before b. Thread t visits the earlier tiles b-1-t, b-1-t-T, ... nearest
+// first, waits at each until it holds its aggregate or its inclusive prefix,
+// and stops at the first inclusive prefix it meets (or below the nearest one
+// another thread has already met, kept in *sh_near). The nearest inclusive
+// prefix J over the block, plus the aggregates of the tiles after J, is the
+// result. Every thread polls at most ceil(b / T) tiles at once, so the walk
+// costs a few rounds of L2 latency however far back J lies. Returns false in
+// every thread when some wait gave up (spin_limit empty polls).
+__device__ __forceinline__ bool block_lookback(const LbStatus *st, uint32_t b, u64 epoch, u64 n,
+                                               uint32_t spin_limit, int *sh_near, u64 *sh_red,
+                                               u64 &excl)
 {
-    const int lane = threadIdx.x & 31;
-    u64 acc = 0;
-    long long top = (long long)b - 1;
-    uint32_t empty_rounds = 0;
-    for (;;) {
-        const long long idx = top - lane;
-        u64 v = 0;
-        int kind = idx < 0 ? 2 : 0;  // 2: inclusive prefix, 1: aggregate, 0: nothing yet
+    const int t = threadIdx.x, T = blockDim.x;
+    bool ok = true;
+    long long j = (long long)b - 1 - t;
+    for (; j >= 0; j -= T) {
+        if (j < *(volatile int *)sh_near)
+            break;  // another thread holds a nearer inclusive prefix
+        uint32_t empty = 0;
+        int kind = 0;
         for (;;) {
-            if (kind == 0) {
-                if (ld_acquire(&st[idx].incl_tag) == epoch) {
-                    v = ld_relaxed(&st[idx].incl);
-                    kind = 2;
-                } else if (ld_acquire(&st[idx].agg_tag) == epoch) {
-                    v = ld_relaxed(&st[idx].agg);
-                    kind = 1;
-                }
-            }
-            if (__all_sync(FULL, kind != 0))
+            if (ld_acquire(&st[j].incl_tag) == epoch) {
+                kind = 2;
                 break;
-            if (empty_rounds >= spin_limit)
-                return false;
-            empty_rounds++;
+            }
+            if (ld_acquire(&st[j].agg_tag) == epoch) {
+                kind = 1;
+                break;
+            }
+            if (empty >= spin_limit) {
+                ok = false;
+                break;
+            }
+            empty++;
             __nanosleep(64);
         }
-        const unsigned pm = __ballot_sync(FULL, kind == 2);
-        const int stop = pm ? __ffs(pm) - 1 : 31;
-        u64 x = lane <= stop ? v : 0;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1)
-            x = addmod(x, __shfl_xor_sync(FULL, x, d), n);
-        acc = addmod(acc, x, n);
-        if (pm)
+        if (!ok)
             break;
-        top -= 32;
+        if (kind == 2) {
+            atomicMax(sh_near, (int)j);
+            break;
+        }
     }
-    excl = acc;
+    if (__syncthreads_or(!ok))
+        return false;
+    const long long J = *(volatile int *)sh_near;  // >= 0: tile 0 only ever publishes its prefix
+    // The aggregates of this thread's tiles after J (each was seen above with
+    // its tag), and the inclusive prefix of J from the thread that owns it.
+    u64 sum = 0;
+    for (long long k = (long long)b - 1 - t; k > J; k -= T)
+        sum = addmod(sum, ld_relaxed(&st[k].agg), n);
+    if (J >= 0 && ((long long)b - 1 - J) % T == t)
+        sum = addmod(sum, ld_relaxed(&st[J].incl), n);
+    excl = tile::block_reduce_mod(sum, n, sh_red);
     return true;
 }
 
@@ -142,8 +153,9 @@ __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbA
 {
     extern __shared__ u64 smem[];
     __shared__ u64 sh_scan[32];
-    __shared__ u64 sh_m0, sh_s0, sh_carry;
-    __shared__ uint32_t sh_b, sh_fail;
+    __shared__ u64 sh_m0, sh_s0;
+    __shared__ uint32_t sh_b;
+    __shared__ int sh_near;
     const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
     const int S = T * L;
     const int slots = S + (S >> 4);
@@ -157,7 +169,7 @@ __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbA
         sh_b = (uint32_t)(atomicAdd(A.ticket, 1ull) - A.ticket_base);
         sh_m0 = tab.state_m[A.inst];
         sh_s0 = tab.state_s[A.inst];
-        sh_fail = 0;
+        sh_near = -1;
     }
     __syncthreads();
     const uint32_t b = sh_b;
@@ -196,31 +208,26 @@ __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbA
     // The tile's block scan, then the look-back for its carry-in.
     auto scan = [&](u64 v, u64 n, u64 &total) -> u64 {
         const u64 pre = tile::block_exscan_mod(v, n, sh_scan, total);
-        if (t < 32) {
-            LbStatus *me = A.status + b;
-            u64 excl = 0;
-            bool ok = true;
-            if (b > 0) {
-                if (lane == 0) {
-                    st_relaxed(&me->agg, total);
-                    st_release(&me->agg_tag, A.epoch);
-                }
-                ok = lookback(A.status, b, A.epoch, n, A.spin_limit, excl);
+        LbStatus *me = A.status + b;
+        u64 excl = 0;
+        bool ok = true;
+        if (b > 0) {
+            if (t == 0) {
+                st_relaxed(&me->agg, total);
+                st_release(&me->agg_tag, A.epoch);
             }
-            if (lane == 0) {
-                if (ok && !(b == 0 && (A.inject & 1))) {
-                    st_relaxed(&me->incl, addmod(excl, total, n));
-                    st_release(&me->incl_tag, A.epoch);
-                }
-                if (!ok)
-                    atomicOr(A.err, 1u);
-                sh_carry = excl;
-                sh_fail = ok ? 0u : 1u;
-            }
+            ok = block_lookback(A.status, b, A.epoch, n, A.spin_limit, &sh_near, sh_scan, excl);
         }
-        __syncthreads();
-        failed = sh_fail != 0;
-        carry = sh_carry;
+        if (t == 0) {
+            if (ok && !(b == 0 && (A.inject & 1))) {
+                st_relaxed(&me->incl, addmod(excl, total, n));
+                st_release(&me->incl_tag, A.epoch);
+            }
+            if (!ok)
+                atomicOr(A.err, 1u);
+        }
+        failed = !ok;
+        carry = excl;
         if (failed)
             W.flags = 0;  // no state write-back after a wait that gave up
         return addmod(carry, pre, n);

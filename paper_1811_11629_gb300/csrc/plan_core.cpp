@@ -110,8 +110,14 @@ uint64_t vec_pieces_per_stream(uint64_t units, uint64_t grid, uint64_t max_piece
 int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const PlanGeometry &geo,
                     uint64_t nreq, const uint32_t *ids, const uint64_t *counts,
                     const uint64_t *offsets, uint64_t chunk, HostPlan &hp, uint64_t tuple,
-                    uint64_t stride)
+                    uint64_t stride, uint64_t pack)
 {
+    if (stride > 1 || tuple > 1 || pack < 1)
+        pack = 1;
+    if (pack > 1 && (geo.threads % pack != 0 || geo.threads / pack < 32))
+        return fail(RSAPRNG_ERR_ARG, "streams per block: %llu does not divide %llu threads into "
+                                     "whole warps", (unsigned long long)pack,
+                    (unsigned long long)geo.threads);
     hp.items.clear();
     hp.chunks.clear();
     hp.groups.clear();
@@ -178,7 +184,11 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         hp.vec_ts = (int)(geo.threads / bestG);
         tile = (uint64_t)hp.vec_ts * geo.L;
     }
-    const uint64_t piece_cost = std::max<uint64_t>(1, work / (geo.grid * kPiecesPerBlock));
+    if (pack > 1) {  // packed streams: a piece runs on threads / pack threads
+        hp.vec_ts = (int)(geo.threads / pack);
+        tile = (uint64_t)hp.vec_ts * geo.L;
+    }
+    const uint64_t piece_cost = std::max<uint64_t>(1, work / (geo.grid * kPiecesPerBlock * pack));
     if (tuple > 1 && chunk != ~0ULL)
         chunk = std::max(tile, chunk / tile * tile);
     struct Piece {
@@ -268,6 +278,19 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
             for (size_t i = 0; i < ni; i++)
                 perm[start[item_rank[i]]++] = (uint32_t)i;
         }
+    } else if (pack > 1) {
+        // Packed streams share a block's tile loop, which runs as long as the
+        // group's longest piece: pieces of one group should be alike in length.
+        auto longer = [&](uint32_t x, uint32_t y) {
+            return hp.items[x].count != hp.items[y].count ? hp.items[x].count > hp.items[y].count
+                                                          : item_cost[x] > item_cost[y];
+        };
+        perm.resize(ni);
+        for (size_t i = 0; i < ni; i++)
+            perm[i] = (uint32_t)i;
+        ordered = std::is_sorted(perm.begin(), perm.end(), longer);
+        if (!ordered)
+            std::stable_sort(perm.begin(), perm.end(), longer);
     } else {
         ordered = std::is_sorted(item_cost.begin(), item_cost.end(),
                                  [](uint64_t x, uint64_t y) { return x > y; });
@@ -290,7 +313,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         hp.items.swap(sorted);
         for (auto &pc : hp.chunks)
             pc.item = where[pc.item];
-        if (stride > 1) {  // the vector units below read rank and cost in the new order
+        if (stride > 1 || pack > 1) {  // the units below read rank and cost in the new order
             std::vector<uint64_t> &tmp = hp.tmp.order;
             tmp.resize(ni);
             for (size_t i = 0; i < ni; i++)
@@ -336,6 +359,32 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         if (out.size() > 0xFFFFFFF0ULL)
             return fail(RSAPRNG_ERR_ARG, "plan too large");
         hp.chunks.swap(out);
+    }
+    if (pack > 1) {
+        // Groups of pack pieces in length order; a group costs its longest
+        // piece at its costliest exponent (the segments share the tile loop).
+        std::vector<uint64_t> &unit_cost = hp.tmp.order;
+        unit_cost.clear();
+        for (uint32_t i = 0; i < (uint32_t)hp.items.size(); i += (uint32_t)pack) {
+            const uint32_t n = (uint32_t)std::min<uint64_t>(pack, hp.items.size() - i);
+            uint64_t w = 0;
+            for (uint32_t k = i; k < i + n; k++)
+                w = std::max(w, item_cost[k] / std::max<uint64_t>(1, hp.items[k].count));
+            hp.vecs.push_back({i, n});
+            unit_cost.push_back(hp.items[i].count * w);
+        }
+        std::vector<uint32_t> &uperm = hp.tmp.perm;
+        uperm.resize(hp.vecs.size());
+        for (uint32_t u = 0; u < (uint32_t)uperm.size(); u++)
+            uperm[u] = u;
+        auto costlier = [&](uint32_t x, uint32_t y) { return unit_cost[x] > unit_cost[y]; };
+        if (!std::is_sorted(uperm.begin(), uperm.end(), costlier)) {
+            std::stable_sort(uperm.begin(), uperm.end(), costlier);
+            std::vector<VecGroup> sorted_vecs(uperm.size());
+            for (size_t u = 0; u < uperm.size(); u++)
+                sorted_vecs[u] = hp.vecs[uperm[u]];
+            hp.vecs.swap(sorted_vecs);
+        }
     }
     if (stride > 1) {
         // Units of the vector kernel: up to G items in a row with the same

@@ -66,11 +66,15 @@ uint64_t vec_pieces_per_stream(uint64_t units, uint64_t grid, uint64_t max_piece
 // cap; with tuple > 1 the cap is rounded down to whole units of tile x tuple,
 // at least one unit); pieces after an instance's first get their start state from the
 // skip-sum pre-pass (chunks, groups). Items are ordered longest first, or by
-// position when stride > 1 (then grouped into VecGroups). params has ninst
-// entries. Errors: RSAPRNG_ERR_ID, RSAPRNG_ERR_ARG.
+// position when stride > 1 (then grouped into VecGroups). With stride 1 and
+// pack > 1 (streams per block, geo.threads / pack a whole number of warps)
+// pieces are cut in tiles of geo.threads / pack threads, ordered by length
+// (longest first) and grouped pack at a time into VecGroups, the groups
+// ordered by cost (longest piece times costliest exponent), costliest first.
+// params has ninst entries. Errors: RSAPRNG_ERR_ID, RSAPRNG_ERR_ARG.
 int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const PlanGeometry &geo,
                     uint64_t nreq, const uint32_t *ids, const uint64_t *counts,
                     const uint64_t *offsets, uint64_t chunk, HostPlan &hp, uint64_t tuple = 1,
-                    uint64_t stride = 1);
+                    uint64_t stride = 1, uint64_t pack = 1);
 
 }  // namespace rsaprng

@@ -1,8 +1,13 @@
 // Launch plans, CUDA-graph capture, host-buffer generation and the autotuner.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "api_internal.hpp"
@@ -20,6 +25,40 @@ struct rsaprng_plan {
 
 namespace {
 
+// Tuned configurations, kept per (device, workload signature, exponent
+// class) for the life of the process (and across processes through
+// rsaprng_autotune_cache_save / _load).
+std::mutex g_tune_mu;
+std::map<std::string, rsaprng_config> g_tune_cache;
+
+// The cache key. Device: compute capability and SM count. Workload: the
+// request count, mean and longest request (log2 buckets) and the output
+// kind. Exponent class: the mean cost per output in Montgomery products
+// (the planner's weight), in steps of two.
+std::string tune_key(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const uint64_t *counts)
+{
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+    uint64_t total = 0, longest = 0;
+    double w = 0;
+    for (uint64_t i = 0; i < nreq; i++) {
+        total += counts[i];
+        longest = std::max(longest, counts[i]);
+        if (ids[i] < c->count) {
+            const InstParams &P = c->h_params[ids[i]];
+            w += (double)counts[i] * (double)cost_per_number(std::max(P.e, P.eq));
+        }
+    }
+    auto lg = [](double x) { return x >= 1 ? (int)std::floor(std::log2(x)) : -1; };
+    const double mean = nreq ? (double)total / (double)nreq : 0.0;
+    const int eclass = total ? (int)(w / (double)total / 2.0) : 0;
+    char buf[160];
+    snprintf(buf, sizeof buf, "sm%d%d-x%d/req2^%d-mean2^%d-max2^%d/rounding%d/e%d", major, minor,
+             c->sms, lg((double)nreq), lg(mean), lg((double)longest), c->cfg.rounding, eclass);
+    return buf;
+}
+
 void destroy_graph(rsaprng_plan *p)
 {
     if (p->exec)
@@ -35,7 +74,7 @@ int plan_create_cfg(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, co
 {
     cudaSetDevice(c->device);
     HostPlan hp;
-    int rc = build_plan(c, cfg, nreq, ids, counts, offsets, cfg.chunk, hp);
+    int rc = build_plan(c, cfg, nreq, ids, counts, offsets, cfg.chunk, hp, 1, 1, true);
     if (rc)
         return rc;
     rsaprng_plan *p = new (std::nothrow) rsaprng_plan();
@@ -405,23 +444,65 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
             best = cfg;
         }
     }
+    // A candidate replaces the best only when it is faster by more than
+    // `margin` (timing noise of a few percent must not move the later, finer
+    // knobs away from their defaults).
+    auto consider = [&](const rsaprng_config &cfg, float margin) {
+        if (rc)
+            return;
+        float ms;
+        if ((rc = trial(cfg, &ms)) != RSAPRNG_OK)
+            return;
+        if (ms < best_ms * (1.0f - margin)) {
+            best_ms = ms;
+            best = cfg;
+        }
+    };
+    // Stage 2: tilings (threads per block, numbers per thread) for the best route.
     const int tiles[][2] = {{128, 4},  {128, 8}, {128, 16}, {256, 4}, {256, 8},
                             {256, 16}, {512, 2}, {512, 4},  {512, 8}};
     for (auto &tl : tiles) {
-        if (rc)
-            break;
         if (tl[1] == 16 && best.modexp == RSAPRNG_MODEXP_MONT64)
             continue;
         rsaprng_config cfg = best;
         cfg.threads_per_block = tl[0];
         cfg.numbers_per_thread = tl[1];
-        float ms;
-        if ((rc = trial(cfg, &ms)) != RSAPRNG_OK)
-            break;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = cfg;
+        consider(cfg, 0.0f);
+    }
+    // Stage 3: unroll, the chains a thread runs at once (passes of half its numbers).
+    {
+        const GenLaunch g = ctx_launch(c, best, ~0ULL, true, false);
+        if (g.L >= 4 && gen_has_unroll(g.L, g.modexp, g.divide, g.L / 2)) {
+            rsaprng_config cfg = best;
+            cfg.unroll = g.L / 2;
+            consider(cfg, 0.02f);
         }
+    }
+    // Stage 4: streams per block (instances side by side, whole warps each).
+    for (int spb : {2, 4}) {
+        if (best.threads_per_block / spb < 32)
+            continue;
+        rsaprng_config cfg = best;
+        cfg.streams_per_block = spb;
+        consider(cfg, 0.02f);
+    }
+    // Stage 5: resident blocks per SM below the occupancy limit.
+    {
+        int occ = 0;
+        (void)ctx_launch(c, best, ~0ULL, true, false, &occ);
+        for (int k = 1; k <= 2 && occ - k >= 1; k++) {
+            rsaprng_config cfg = best;
+            cfg.blocks_per_sm = occ - k;
+            consider(cfg, 0.02f);
+        }
+    }
+    // Stage 6: the chunk cap of long streams.
+    for (uint64_t ch : {1ULL << 16, 1ULL << 17, 1ULL << 19, 1ULL << 20}) {
+        if (ch == best.chunk)
+            continue;
+        rsaprng_config cfg = best;
+        cfg.chunk = ch;
+        consider(cfg, 0.02f);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -433,6 +514,116 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
     c->cfg = best;
     if (chosen)
         *chosen = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(c, nreq, ids, counts)] = best;
+    return RSAPRNG_OK;
+}
+
+int rsaprng_autotune_cached(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids,
+                            const uint64_t *counts, int reps, rsaprng_config *chosen,
+                            int *from_cache)
+{
+    if (!c || !nreq || !ids || !counts)
+        return fail(RSAPRNG_ERR_ARG, "autotune: bad arguments");
+    if (from_cache)
+        *from_cache = 0;
+    const std::string key = tune_key(c, nreq, ids, counts);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            rsaprng_config cfg = it->second;
+            // keep the context's own switches; take the tuned knobs
+            cfg.require_safe = c->cfg.require_safe;
+            cfg.lookback = c->cfg.lookback;
+            cfg.spin_limit = c->cfg.spin_limit;
+            cfg.test_flags = c->cfg.test_flags;
+            c->cfg = cfg;
+            if (chosen)
+                *chosen = cfg;
+            if (from_cache)
+                *from_cache = 1;
+            return RSAPRNG_OK;
+        }
+    }
+    return rsaprng_autotune(c, nreq, ids, counts, reps, chosen);
+}
+
+uint64_t rsaprng_autotune_cache_size(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune_cache.size();
+}
+
+void rsaprng_autotune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+}
+
+// One line per entry: the key, then the tuned knobs as name=value pairs.
+int rsaprng_autotune_cache_save(const char *path)
+{
+    if (!path)
+        return fail(RSAPRNG_ERR_ARG, "autotune cache: null path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE *f = fopen(path, "w");
+    if (!f)
+        return fail(RSAPRNG_ERR_ARG, "autotune cache: cannot write %s", path);
+    for (const auto &kv : g_tune_cache) {
+        const rsaprng_config &k = kv.second;
+        fprintf(f, "%s modexp=%d divide=%d threads=%d numbers=%d blocks_per_sm=%d chunk=%llu "
+                   "streams_per_block=%d unroll=%d rounding=%d\n",
+                kv.first.c_str(), k.modexp, k.divide, k.threads_per_block, k.numbers_per_thread,
+                k.blocks_per_sm, (unsigned long long)k.chunk, k.streams_per_block, k.unroll,
+                k.rounding);
+    }
+    const bool ok = fclose(f) == 0;
+    return ok ? RSAPRNG_OK : fail(RSAPRNG_ERR_ARG, "autotune cache: write failed");
+}
+
+int rsaprng_autotune_cache_load(const char *path)
+{
+    if (!path)
+        return fail(RSAPRNG_ERR_ARG, "autotune cache: null path");
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return fail(RSAPRNG_ERR_ARG, "autotune cache: cannot read %s", path);
+    std::map<std::string, rsaprng_config> got;
+    char key[256];
+    int modexp, divide, threads, numbers, bps, spb, unroll, rounding;
+    unsigned long long chunk;
+    int rc = RSAPRNG_OK;
+    for (;;) {
+        const int n = fscanf(f, "%255s modexp=%d divide=%d threads=%d numbers=%d blocks_per_sm=%d "
+                                "chunk=%llu streams_per_block=%d unroll=%d rounding=%d",
+                             key, &modexp, &divide, &threads, &numbers, &bps, &chunk, &spb,
+                             &unroll, &rounding);
+        if (n == EOF)
+            break;
+        if (n != 10) {
+            rc = fail(RSAPRNG_ERR_ARG, "autotune cache: malformed line in %s", path);
+            break;
+        }
+        rsaprng_config k{};
+        k.struct_size = sizeof k;
+        k.modexp = modexp;
+        k.divide = divide;
+        k.threads_per_block = threads;
+        k.numbers_per_thread = numbers;
+        k.blocks_per_sm = bps;
+        k.chunk = chunk;
+        k.streams_per_block = spb;
+        k.unroll = unroll;
+        k.rounding = rounding;
+        got[key] = k;
+    }
+    fclose(f);
+    if (rc)
+        return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : got)
+        g_tune_cache[kv.first] = kv.second;
     return RSAPRNG_OK;
 }
 

@@ -311,7 +311,7 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     HostPlan hp;
     cudaEventRecord(sl.start, sl.stream);
     int rc = build_plan(S->ctx, S->ctx->cfg, ids.size(), ids.data(), counts.data(), offs.data(),
-                        chunk, hp);
+                        chunk, hp, 1, 1, true);
     if (rc == RSAPRNG_OK)
         rc = upload_plan(S->ctx, hp, sl.plan, sl.stream);
     if (rc == RSAPRNG_OK)

@@ -91,6 +91,34 @@ __device__ __forceinline__ void encrypt(const u64 (&m)[L], u64 (&c)[L], const In
         dev::encrypt_mont64<L>(m, c, P);
 }
 
+// Encryption of a thread's L messages with at most U chains in flight: the
+// L outputs run as L / U passes of U, and each pass takes an opaque zero
+// computed from the last ciphertext of the pass before it, so the compiler
+// cannot start a pass before the previous one has finished (fewer live
+// registers, less instruction-level parallelism). U >= L: all at once.
+template <int L, int MODEXP, int U>
+__device__ __forceinline__ void encrypt_passes(const u64 (&m)[L], u64 (&c)[L], const InstParams &P)
+{
+    if constexpr (U >= L) {
+        encrypt<L, MODEXP>(m, c, P);
+    } else {
+        static_assert(L % U == 0, "passes of equal size");
+        u64 dep = 0;
+#pragma unroll
+        for (int g = 0; g < L / U; g++) {
+            u64 mm[U], cc[U];
+#pragma unroll
+            for (int j = 0; j < U; j++)
+                mm[j] = m[g * U + j] + dep;  // messages are representatives: + 0 changes nothing
+            encrypt<U, MODEXP>(mm, cc, P);
+#pragma unroll
+            for (int j = 0; j < U; j++)
+                c[g * U + j] = cc[j];
+            asm volatile("and.b64 %0, %1, 0;" : "=l"(dep) : "l"(cc[U - 1]));
+        }
+    }
+}
+
 // Division route for output j of a thread's run.
 template <int DIV>
 __device__ __forceinline__ double to_unit(u64 c, const InstParams &P, int j)
@@ -124,6 +152,39 @@ __device__ __forceinline__ u64 segment_exscan_mod(u64 v, u64 n, int TS, u64 &tot
     return lt == 0 ? 0 : ex;
 }
 
+// The same over segments of TS consecutive threads that are whole warps (TS
+// a multiple of 32 and a power of two): a warp scan, then the totals of the
+// segment's earlier warps from shared memory. sh holds 32 entries; one
+// barrier (the caller keeps sh untouched until its next barrier).
+__device__ __forceinline__ u64 segment_exscan_mod_warps(u64 v, u64 n, int TS, u64 *sh,
+                                                        u64 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const u64 o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d)
+            incl = addmod(incl, o, n);
+    }
+    if (lane == 31)
+        sh[warp] = incl;
+    __syncthreads();
+    const int wps = TS >> 5, w0 = warp - (warp & (wps - 1));
+    u64 wpre = 0, tot = 0;
+    for (int w = w0; w < w0 + wps; w++) {
+        const u64 x = sh[w];
+        if (w < warp)
+            wpre = addmod(wpre, x, n);
+        tot = addmod(tot, x, n);
+    }
+    total = tot;
+    u64 ex = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0)
+        ex = 0;
+    return addmod(wpre, ex, n);
+}
+
 // Steps 1-3 of a tile for the calling thread, which owns outputs my0+1 ..
 // my0+L of its stream's tile: its skips from s_thr (the skip before its run),
 // the scan of their sums mod n over the threads of the stream (scan(sum, n,
@@ -133,7 +194,7 @@ __device__ __forceinline__ u64 segment_exscan_mod(u64 v, u64 n, int TS, u64 &tot
 // output (left = outputs from the tile start to the end of the work item)
 // writes the instance's skip back when the item asks for it. total returns
 // the tile's skip sum mod n (the carry to the next tile).
-template <int L, int MODEXP, class Scan>
+template <int L, int MODEXP, class Scan, int U = L>
 __device__ __forceinline__ void tile_ciphertexts_scan(const DeviceTables &tab, const WorkItem &W,
                                                       const InstParams &P, u64 m, u64 s_thr,
                                                       u64 left, int my0, int nvalid, Scan &&scan,
@@ -163,20 +224,20 @@ __device__ __forceinline__ void tile_ciphertexts_scan(const DeviceTables &tab, c
     }
     if ((W.flags & WI_WRITEBACK) && nvalid > 0 && (u64)(my0 + nvalid) == left)
         tab.state_s[W.inst] = s_last;  // this thread owns the stream's last output
-    encrypt<L, MODEXP>(msg, c, P);
+    encrypt_passes<L, MODEXP, U>(msg, c, P);
 }
 
 // The same for one stream per block: the block-wide scan (two
 // __syncthreads()).
-template <int L, int MODEXP>
+template <int L, int MODEXP, int U = L>
 __device__ __forceinline__ void tile_ciphertexts(const DeviceTables &tab, const WorkItem &W,
                                                  const InstParams &P, u64 m, u64 s_thr, u64 left,
                                                  int my0, int nvalid, u64 *sh_scan, u64 (&c)[L],
                                                  u64 &total)
 {
-    tile_ciphertexts_scan<L, MODEXP>(
-        tab, W, P, m, s_thr, left, my0, nvalid,
-        [&](u64 v, u64 n, u64 &tot) { return block_exscan_mod(v, n, sh_scan, tot); }, c, total);
+    auto scan = [&](u64 v, u64 n, u64 &tot) { return block_exscan_mod(v, n, sh_scan, tot); };
+    tile_ciphertexts_scan<L, MODEXP, decltype(scan) &, U>(tab, W, P, m, s_thr, left, my0, nvalid,
+                                                       scan, c, total);
 }
 
 }  // namespace tile

@@ -13,6 +13,12 @@
 // The plan is the ordinary one (pieces, skip-sum pre-pass, start states);
 // the host groups up to G work items that cover the same positions of
 // consecutive instances of a vector into one block's unit (VecGroup).
+//
+// The same kernel packs unrelated streams into a block (stride 1): G pieces
+// of any instances and lengths, TS = T / G threads each (whole warps, so no
+// warp mixes exponents), the group's first piece the longest. The block runs
+// the tiles of its longest piece; a segment whose piece has ended computes on
+// with nothing valid, and each segment writes its own run contiguously.
 #include "device_math.cuh"
 #include "kernels.cuh"
 #include "tile.cuh"
@@ -36,6 +42,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
 {
     tile::pdl_wait();  // the start states of the pieces, from the start-state scan
     extern __shared__ u64 smem[];
+    __shared__ u64 sh_scan[32];
     __shared__ uint32_t sh_item;
     const int T = TB ? TB : (int)blockDim.x, t = threadIdx.x;
     const int tsh = __ffs(TS) - 1, G = T >> tsh, gsh = __ffs(G) - 1;  // both powers of two
@@ -75,16 +82,22 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
         }
         u64 s_thr = mulmodQ(s, plin[my0]);
         const u64 aK = plin[K];
-        const u64 count = W.count;  // the same for every item of the group
+        // This segment's length, and the group's (its first item is the
+        // longest); in the interleaved order they are all equal.
+        const u64 count = W.count;
+        const u64 gcount = items[V.first].count;
         const u64 o0 = items[V.first].out_off;
-        for (u64 base = 0; base < count; base += K) {
-            const u64 left = count - base;
+        for (u64 base = 0; base < gcount; base += K) {
+            const u64 left = count > base ? count - base : 0;
             const int tile_n = left < (u64)K ? (int)left : K;
             const int nvalid = !on ? 0 : (tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0));
             u64 c[L], total;
             tile::tile_ciphertexts_scan<L, MODEXP>(
                 tab, W, P, m, s_thr, left, my0, nvalid,
-                [&](u64 x, u64 nn, u64 &tot) { return tile::segment_exscan_mod(x, nn, TS, tot); },
+                [&](u64 x, u64 nn, u64 &tot) {
+                    return TS <= 32 ? tile::segment_exscan_mod(x, nn, TS, tot)
+                                    : tile::segment_exscan_mod_warps(x, nn, TS, sh_scan, tot);
+                },
                 c, total);
             // staged by instance: slot seg K + position (padded every 16)
             const int row0 = seg * K + my0;
@@ -96,9 +109,22 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
                     st_c[sidx(row0 + j)] = c[j];
             }
             __syncthreads();
-            // Written k-major: T is a multiple of G, so thread t always writes
-            // column t mod G, at positions t / G, t / G + TS, ...
-            if (wcol < (int)V.count) {
+            if (stride == 1) {
+                // Packed streams: each segment's run is contiguous at its own
+                // offset, written by its TS threads.
+                if (on) {
+                    const u64 o = W.out_off + base;
+                    for (int k = lt; k < tile_n; k += TS) {
+                        const int slot = sidx(seg * K + k);
+                        if (out_r)
+                            out_r[o + k] = __longlong_as_double((long long)st_r[slot]);
+                        if (out_c)
+                            out_c[o + k] = st_c[slot];
+                    }
+                }
+            } else if (wcol < (int)V.count) {
+                // Written k-major: T is a multiple of G, so thread t always
+                // writes column t mod G, at positions t / G, t / G + TS, ...
                 u64 e = o0 + (base + (u64)wk0) * stride + (u64)wcol;
                 const u64 step = (u64)TS * stride;
                 for (int k = wk0; k < tile_n; k += TS, e += step) {

@@ -8,7 +8,9 @@
 //     listed as skip-sum chunks (the last with length 0) in stream order;
 //  3. pieces start on tiles (and on multiples of the tuple), respect the
 //     chunk cap, and are ordered longest first (or by position for stride > 1);
-//  4. vector groups partition the items into runs of neighbours;
+//  4. vector groups partition the items into runs of neighbours; packed
+//     groups (several streams per block) partition them into runs of at most
+//     `pack` items in length order, ordered by cost;
 //  5. unknown ids and CRT exponents on the 64-bit route are refused.
 // Exit status 0 when every case passes.
 #include <algorithm>
@@ -100,9 +102,13 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
     const uint64_t chunk_opts[] = {0, 1ULL << 12, 1ULL << 16, 5000, 1ULL << 18};
     const uint64_t chunk = chunk_opts[rng() % 5];
     const int modexp = (rng() % 4 == 0) ? RSAPRNG_MODEXP_MONT64 : RSAPRNG_MODEXP_CRT32;
+    // streams per block for contiguous plans: whole warps per stream
+    uint64_t pack = 1;
+    if (stride == 1 && tuple == 1 && rng() % 2)
+        pack = std::min<uint64_t>(1ULL << (rng() % 4), geo.threads / 32);
     HostPlan hp;
     const int rc = build_plan_core(params.data(), ninst, modexp, geo, ids.size(), ids.data(),
-                                   counts.data(), offsets.data(), chunk, hp, tuple, stride);
+                                   counts.data(), offsets.data(), chunk, hp, tuple, stride, pack);
     bool split_e = false;
     for (uint32_t id : ids)
         split_e |= params[id].e != params[id].eq;
@@ -194,7 +200,9 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
     }
     // 3. order of the items
     for (size_t k = 1; k < hp.items.size(); k++) {
-        if (stride == 1) {
+        if (pack > 1) {
+            CHECK(hp.items[k - 1].count >= hp.items[k].count, "packed pieces not by length");
+        } else if (stride == 1) {
             auto cost = [&](const WorkItem &w) {
                 return w.count *
                        cost_per_number(std::max(params[w.inst].e, params[w.inst].eq));
@@ -238,6 +246,28 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
             covered += g.count;
         }
         CHECK(covered == hp.items.size(), "groups cover %llu of %zu items",
+              (unsigned long long)covered, hp.items.size());
+    } else if (pack > 1) {
+        CHECK(hp.vec_ts == (int)(geo.threads / pack), "packed threads per stream %d", hp.vec_ts);
+        std::vector<int> seen(hp.items.size(), 0);
+        uint64_t covered = 0, prev_cost = ~0ULL;
+        for (const auto &g : hp.vecs) {
+            CHECK(g.count >= 1 && g.count <= pack && g.first % pack == 0 &&
+                      (uint64_t)g.first + g.count <= hp.items.size() &&
+                      (g.count == pack || (uint64_t)g.first + g.count == hp.items.size()),
+                  "packed group layout");
+            uint64_t w = 0;
+            for (uint32_t j = 0; j < g.count; j++) {
+                CHECK(!seen[g.first + j]++, "item in two groups");
+                const WorkItem &b = hp.items[g.first + j];
+                w = std::max(w, cost_per_number(std::max(params[b.inst].e, params[b.inst].eq)));
+            }
+            const uint64_t cost = hp.items[g.first].count * w;
+            CHECK(cost <= prev_cost, "packed groups not costliest first");
+            prev_cost = cost;
+            covered += g.count;
+        }
+        CHECK(covered == hp.items.size(), "packed groups cover %llu of %zu items",
               (unsigned long long)covered, hp.items.size());
     } else {
         CHECK(hp.vecs.empty(), "vector groups in a contiguous plan");

@@ -112,6 +112,44 @@ def test_routes_and_tilings_ragged(O, modexp, divide, threads, L):
             off += n
 
 
+@pytest.mark.parametrize("cfg", [
+    dict(streams_per_block=2), dict(streams_per_block=4),
+    dict(streams_per_block=2, threads_per_block=256), dict(streams_per_block=8, threads_per_block=256),
+    dict(streams_per_block=4, divide=R.DIVIDE_INT), dict(streams_per_block=2, modexp=R.MODEXP_MONT64,
+                                                        numbers_per_thread=8),
+    dict(unroll=8), dict(unroll=8, divide=R.DIVIDE_HYBRID), dict(unroll=8, divide=R.DIVIDE_INT),
+    dict(unroll=4, numbers_per_thread=8), dict(unroll=2),  # the last: no variant, all at once
+    dict(unroll=8, streams_per_block=2, chunk=4096),
+])
+def test_packed_streams_and_chain_passes(O, cfg):
+    """The autotuner's knobs: several streams per block (segments of whole warps, pieces of
+    different lengths side by side) and exponentiation chains in passes. Uneven requests,
+    several per instance, streams cut into pieces, two calls; bit-exact with the oracle."""
+    ctx = R.Context(32, **cfg)
+    ids, par = seeded(ctx, O, master=14, k=12, rule=R.E_UNIFORM, lo=3, hi=257)
+    req = np.concatenate([ids, ids[:5]]).astype(np.uint32)
+    counts = np.array([0, 1, 31, 100, 511, 2047, 2048, 4100, 9000, 33333, 150001, 70, 5,
+                       777, 20000, 1, 65536], np.uint64)
+    states = {int(i): (pr[3], 1) for i, pr in zip(ids, par)}
+    pmap = {int(i): pr for i, pr in zip(ids, par)}
+    for call in range(2):
+        total = int(counts.sum())
+        out_c = torch.full((total + 1,), 7, dtype=torch.int64, device="cuda")
+        out_r = torch.full((total + 1,), -1.0, dtype=torch.float64, device="cuda")
+        ctx.generate_batch(req, counts, out_r=out_r, out_c=out_c)
+        torch.cuda.synchronize()
+        gc, gr = out_c.cpu().numpy().view(np.uint64), out_r.cpu().numpy()
+        assert gc[total] == 7 and gr[total] == -1.0
+        off = 0
+        for i in range(len(req)):
+            iid, n = int(req[i]), int(counts[i])
+            states[iid] = check_stream(O, pmap[iid], *states[iid], gc[off:off + n],
+                                       gr[off:off + n])
+            off += n
+        for iid in states:
+            assert ctx.get_state(iid) == states[iid]
+
+
 def test_chunked_streams_and_fifo_requests(O):
     """Long streams cut into chunks (skip-sum pre-pass) and several requests per instance."""
     ctx = R.Context(8, chunk=4096 * 3, threads_per_block=256, numbers_per_thread=4)
@@ -390,6 +428,43 @@ def test_autotune_bit_identical_and_state_preserved(O):
     g = out.cpu().numpy()
     for i in range(len(ids)):
         check_stream(O, par[i], par[i][3], 1, None, g[i * 20000:(i + 1) * 20000])
+
+
+def test_autotune_cache(O, tmp_path):
+    """The tuning cache: a miss tunes, the same workload signature hits and applies the same
+    knobs at once, and a saved cache loads into a cleared one; outputs stay bit-exact."""
+    L = R._lib.load()
+    L.rsaprng_autotune_cache_clear()
+    ctx = R.Context(64)
+    ids, par = seeded(ctx, O, master=24, k=30, rule=R.E_UNIFORM, lo=3, hi=257)
+    counts = workload.lognormal_lengths(24, len(ids), median=4000.0, sigma=1.0, lo=100, hi=60000)
+    cfg1, hit1 = ctx.autotune_cached(ids, counts, reps=1)
+    assert not hit1 and L.rsaprng_autotune_cache_size() == 1
+    ctx2 = R.Context(64)
+    ids2, _ = seeded(ctx2, O, master=24, k=30, rule=R.E_UNIFORM, lo=3, hi=257)
+    cfg2, hit2 = ctx2.autotune_cached(ids2, counts, reps=1)
+    assert hit2
+    knobs = ("modexp", "divide", "threads_per_block", "numbers_per_thread", "blocks_per_sm",
+             "chunk", "streams_per_block", "unroll")
+    assert {k: cfg1[k] for k in knobs} == {k: cfg2[k] for k in knobs}
+    path = str(tmp_path / "tune.txt")
+    assert L.rsaprng_autotune_cache_save(path.encode()) == 0
+    L.rsaprng_autotune_cache_clear()
+    assert L.rsaprng_autotune_cache_size() == 0
+    assert L.rsaprng_autotune_cache_load(path.encode()) == 0
+    _, hit3 = ctx2.autotune_cached(ids2, counts, reps=1)
+    assert hit3
+    total = int(counts.sum())
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    ctx2.generate_batch(ids2, counts, out_r=out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    off = 0
+    for i in range(len(ids2)):
+        n = int(counts[i])
+        check_stream(O, par[i], par[i][3], 1, None, g[off:off + n])
+        off += n
+    L.rsaprng_autotune_cache_clear()
 
 
 @pytest.mark.parametrize("r_mem,c_mem", [("pinned", "pageable"), ("pinned", "pinned"),

@@ -105,3 +105,29 @@ def test_chi2_uniform_host_helper(R):
     assert R.chi2_uniform(flat) == (0.0, 576)
     with pytest.raises(R.RsaPrngError):
         R.chi2_uniform(np.zeros(8, np.uint64))
+
+
+def test_autotune_cache_file_round_trip(R, tmp_path):
+    """The tuning cache's text file (no GPU needed): entries load, save back line for
+    line, and a malformed file is refused without touching the entries held."""
+    L = R._lib.load()
+    L.rsaprng_autotune_cache_clear()
+    lines = ["sm103-x152/req2^10-mean2^14-max2^23/rounding0/e6 modexp=1 divide=4 threads=128 "
+             "numbers=16 blocks_per_sm=0 chunk=262144 streams_per_block=2 unroll=8 rounding=0",
+             "sm103-x152/req2^0-mean2^19-max2^19/rounding0/e4 modexp=1 divide=3 threads=256 "
+             "numbers=8 blocks_per_sm=4 chunk=65536 streams_per_block=1 unroll=0 rounding=0"]
+    src = tmp_path / "in.txt"
+    src.write_text("\n".join(lines) + "\n")
+    assert L.rsaprng_autotune_cache_load(str(src).encode()) == 0
+    assert L.rsaprng_autotune_cache_size() == 2
+    out = tmp_path / "out.txt"
+    assert L.rsaprng_autotune_cache_save(str(out).encode()) == 0
+    assert sorted(out.read_text().splitlines()) == sorted(lines)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("key modexp=1 divide=oops\n")
+    assert L.rsaprng_autotune_cache_load(str(bad).encode()) == R._lib.CODES["ERR_ARG"]
+    assert L.rsaprng_autotune_cache_load(str(tmp_path / "missing").encode()) == \
+        R._lib.CODES["ERR_ARG"]
+    assert L.rsaprng_autotune_cache_size() == 2
+    L.rsaprng_autotune_cache_clear()
+    assert L.rsaprng_autotune_cache_size() == 0

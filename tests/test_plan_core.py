@@ -46,6 +46,13 @@ MUTANTS = {
                            "out.push_back({c.inst, c.item, off, l});"),
     "units_cheapest_first": ("return rx != ry ? rx < ry : unit_cost[x] > unit_cost[y];",
                              "return rx != ry ? rx < ry : unit_cost[x] < unit_cost[y];"),
+    "packed_by_cost_not_length": (
+        "return hp.items[x].count != hp.items[y].count ? hp.items[x].count > hp.items[y].count\n"
+        "                                                          : item_cost[x] > item_cost[y];",
+        "return item_cost[x] > item_cost[y];"),
+    "packed_groups_cheapest_first": (
+        "auto costlier = [&](uint32_t x, uint32_t y) { return unit_cost[x] > unit_cost[y]; };",
+        "auto costlier = [&](uint32_t x, uint32_t y) { return unit_cost[x] < unit_cost[y]; };"),
 }
 
 
