@@ -66,6 +66,8 @@ def parse_args(argv=None):
                     help="override numbers per instance (small profiling runs only)")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--per-thread", type=int, default=0)
+    ap.add_argument("--pieces-per-block", type=int, default=0,
+                    help="load-balance pieces per resident block (0: the default, 1)")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="cap on resident generation blocks per SM (0: occupancy limit)")
     ap.add_argument("--modexp", type=int, default=0)
@@ -332,7 +334,7 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
 
 # --------------------------------------------------------------------------- other forms
 TUNED_KEYS = ("modexp", "divide", "threads_per_block", "numbers_per_thread", "blocks_per_sm",
-              "chunk", "streams_per_block", "unroll")
+              "chunk", "streams_per_block", "unroll", "pieces_per_block")
 
 
 def _slots(es, counts) -> float:
@@ -360,11 +362,13 @@ def form_plain(R, torch, device, pk, rank) -> dict:
     dt = a.elapsed_time(b) / 1e3 / reps
     e = ctx.params(first)[2]
     divide = ctx.config()["divide"]
+    # A 1e6 draw fits one wave of the latency shape: 512 x 16 tiles, integer division.
     out = {"value": round(n / dt / 1e9, 3), "unit": UNIT, "ms_per_call": round(dt * 1e3, 4),
-           "e": e, "outputs": "u64+f64", "divide": divide,
+           "e": e, "outputs": "u64+f64", "divide": DIVIDE_INT,
            "hbm_GBps": round(16 * n / dt / 1e9, 1)}
-    out.update(bounds(pk, n, _slots([e], [n]), dt, divide, 16))
-    out["path"] = "one launch, decoupled look-back over the tiles' skip sums"
+    out.update(bounds(pk, n, _slots([e], [n]), dt, DIVIDE_INT, 16))
+    out["path"] = ("one launch, decoupled look-back over the tiles' skip sums, latency shape "
+                   "(512 x 16 tiles, integer division)")
     # The same calls through the chunked path (skip-sum pre-pass, scan, generation).
     ctx.configure(lookback=R.LOOKBACK_OFF)
     for _ in range(3):
@@ -378,6 +382,18 @@ def form_plain(R, torch, device, pk, rank) -> dict:
     dtc = a.elapsed_time(b) / 1e3 / reps
     out["chunked"] = {"value": round(n / dtc / 1e9, 3), "ms_per_call": round(dtc * 1e3, 4),
                       "path": "pre-pass + scan + generation (three launches)"}
+    # One launch in the configured (throughput) shape instead of the latency shape.
+    ctx.configure(lookback=R.LOOKBACK_CONFIGURED)
+    for _ in range(3):
+        ctx.generate_both(first, n, oc, orr)
+    a.record()
+    for _ in range(reps):
+        ctx.generate_both(first, n, oc, orr)
+    b.record()
+    torch.cuda.synchronize()
+    dts = a.elapsed_time(b) / 1e3 / reps
+    out["configured_shape"] = {"value": round(n / dts / 1e9, 3), "ms_per_call": round(dts * 1e3, 4),
+                               "path": "one launch, 128 x 16 reciprocal-division tiles"}
     ctx.configure()
     assert ctx.device_status() == 0
     # The same draw as a plan captured in a CUDA graph (one graph launch per 1e6 outputs).
@@ -636,7 +652,8 @@ def run_ours(args) -> int:
     knobs = {x: y for x, y in (("threads_per_block", args.threads),
                                ("numbers_per_thread", args.per_thread),
                                ("modexp", args.modexp), ("divide", args.divide),
-                               ("blocks_per_sm", args.blocks_per_sm)) if y}
+                               ("blocks_per_sm", args.blocks_per_sm),
+                               ("pieces_per_block", args.pieces_per_block)) if y}
     ctx = R.Context(k, device=dist.local_rank, chunk=n, **knobs)
     first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)

@@ -138,17 +138,24 @@ typedef struct {
                                    two runs them in passes of that many (128 x 16 CRT
                                    tiles with 8, 8-per-thread CRT reciprocal tiles with
                                    4; other tilings run all at once) */
-    int32_t reserved[1];
+    int32_t pieces_per_block;   /* load balance of generation plans: streams whose work
+                                   exceeds 1 / (resident blocks x this) of the launch are
+                                   cut into pieces (each extra piece costs a skip-sum pass
+                                   over the piece before it); 1 by default */
 } rsaprng_config;
 
 enum {
-    RSAPRNG_LOOKBACK_AUTO = 0, /* one launch with a decoupled look-back when the draw is
-                                  at most 4096 tiles and the tiling has such a kernel
-                                  (16 per thread on the CRT route, 8 per thread on the
-                                  CRT route with reciprocal division or on the 64-bit
-                                  route with reciprocal or integer division); else the
-                                  chunked path (skip-sum pre-pass, scan, generation) */
-    RSAPRNG_LOOKBACK_OFF = 1   /* always the chunked path */
+    RSAPRNG_LOOKBACK_AUTO = 0, /* one launch with a decoupled look-back: in the latency
+                                  shape (512 threads x 16 per thread, CRT route, integer
+                                  division) when the draw fits one wave of such blocks,
+                                  else in the configured shape when the draw is at most
+                                  4096 tiles and the tiling has such a kernel (16 per
+                                  thread on the CRT route, 8 per thread on the CRT route
+                                  with reciprocal division or on the 64-bit route with
+                                  reciprocal or integer division); else the chunked path
+                                  (skip-sum pre-pass, scan, generation) */
+    RSAPRNG_LOOKBACK_OFF = 1,  /* always the chunked path */
+    RSAPRNG_LOOKBACK_CONFIGURED = 2 /* as AUTO without the latency shape */
 };
 
 /* ------------------------------------------------------------- context */

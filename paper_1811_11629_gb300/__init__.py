@@ -12,13 +12,14 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DEFAULT_ROOT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_INT, DIVIDE_RECIP, E_AT_LEAST, E_SMALLEST, E_UNIFORM,
-                   HIST_HIGH, HIST_LOW, LOOKBACK_AUTO, LOOKBACK_OFF,
+                   HIST_HIGH, HIST_LOW, LOOKBACK_AUTO, LOOKBACK_CONFIGURED, LOOKBACK_OFF,
                    MODEXP_CRT32, MODEXP_MONT64, Q, Config, RsaPrngError, Stats, check)
 
 __all__ = ["Context", "Plan", "Server", "Config", "RsaPrngError", "is_prime", "root_allowed",
            "params_from_seed", "Q", "DEFAULT_ROOT", "MODEXP_CRT32", "MODEXP_MONT64",
            "DIVIDE_INT", "DIVIDE_FP64", "DIVIDE_HYBRID", "DIVIDE_RECIP", "E_SMALLEST", "E_UNIFORM", "E_AT_LEAST",
-           "HIST_HIGH", "HIST_LOW", "LOOKBACK_AUTO", "LOOKBACK_OFF", "chi2_uniform"]
+           "HIST_HIGH", "HIST_LOW", "LOOKBACK_AUTO", "LOOKBACK_CONFIGURED", "LOOKBACK_OFF",
+           "chi2_uniform"]
 
 
 def _u64p(a: np.ndarray):

@@ -23,7 +23,7 @@ pvp = ctypes.POINTER(ctypes.c_void_p)
 OK = 0
 MODEXP_AUTO, MODEXP_CRT32, MODEXP_MONT64 = 0, 1, 2
 DIVIDE_AUTO, DIVIDE_INT, DIVIDE_FP64, DIVIDE_HYBRID, DIVIDE_RECIP = 0, 1, 2, 3, 4
-LOOKBACK_AUTO, LOOKBACK_OFF = 0, 1
+LOOKBACK_AUTO, LOOKBACK_OFF, LOOKBACK_CONFIGURED = 0, 1, 2
 E_SMALLEST, E_UNIFORM, E_AT_LEAST = 0, 1, 2
 HIST_HIGH, HIST_LOW = 0, 1
 ROUND_DEFAULT, ROUND_PAPER, ROUND_EXACT = 0, 1, 2
@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
                 ("threads_per_block", i32), ("numbers_per_thread", i32), ("blocks_per_sm", i32),
                 ("chunk", u64), ("require_safe", i32), ("rounding", i32),
                 ("lookback", i32), ("spin_limit", i32), ("test_flags", i32),
-                ("streams_per_block", i32), ("unroll", i32), ("reserved", i32 * 1)]
+                ("streams_per_block", i32), ("unroll", i32), ("pieces_per_block", i32)]
 
 
 class Stats(ctypes.Structure):

@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 static const rsaprng_config kDefaultConfig = {
     sizeof(rsaprng_config), RSAPRNG_MODEXP_CRT32, RSAPRNG_DIVIDE_RECIP, 128, 16, 0, 1ULL << 18, 0,
-    RSAPRNG_ROUND_DEFAULT, RSAPRNG_LOOKBACK_AUTO, 0, 0, 1, 0, {0}};
+    RSAPRNG_ROUND_DEFAULT, RSAPRNG_LOOKBACK_AUTO, 0, 0, 1, 0, 1};
 
 static int check_config(const rsaprng_config &c)
 {
@@ -56,7 +56,7 @@ static int check_config(const rsaprng_config &c)
         return fail(RSAPRNG_ERR_ARG, "config: blocks_per_sm out of range");
     if (c.rounding < 0 || c.rounding > RSAPRNG_ROUND_EXACT)
         return fail(RSAPRNG_ERR_ARG, "config: rounding out of range");
-    if (c.lookback < 0 || c.lookback > RSAPRNG_LOOKBACK_OFF)
+    if (c.lookback < 0 || c.lookback > RSAPRNG_LOOKBACK_CONFIGURED)
         return fail(RSAPRNG_ERR_ARG, "config: lookback out of range");
     if (c.streams_per_block < 0 || c.streams_per_block > 16 ||
         (c.streams_per_block & (c.streams_per_block - 1)))
@@ -66,6 +66,8 @@ static int check_config(const rsaprng_config &c)
         return fail(RSAPRNG_ERR_ARG, "config: streams_per_block leaves a stream less than a warp");
     if (c.unroll < 0 || c.unroll > 16 || (c.unroll & (c.unroll - 1)))
         return fail(RSAPRNG_ERR_ARG, "config: unroll must be 0, 1, 2, 4, 8 or 16");
+    if (c.pieces_per_block < 0 || c.pieces_per_block > 64)
+        return fail(RSAPRNG_ERR_ARG, "config: pieces_per_block out of range");
     return RSAPRNG_OK;
 }
 
@@ -93,6 +95,8 @@ static rsaprng_config merged(const rsaprng_config &base, const rsaprng_config *o
         c.streams_per_block = over->streams_per_block;
     if (over->unroll)
         c.unroll = over->unroll;
+    if (over->pieces_per_block)
+        c.pieces_per_block = over->pieces_per_block;
     c.lookback = over->lookback;
     c.spin_limit = over->spin_limit;
     c.test_flags = over->test_flags;
@@ -175,7 +179,8 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
                               : 1;
     const GenLaunch full = (stride > 1 || pack > 1) ? vec_launch(c, cfg, ~0ULL, true, false)
                                                     : ctx_launch(c, cfg, ~0ULL, true, false);
-    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid};
+    const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid,
+                           (uint64_t)std::max(1, cfg.pieces_per_block)};
     return build_plan_core(c->h_params.data(), c->count, cfg.modexp, geo, nreq, ids, counts,
                            offsets, chunk, hp, tuple, stride, pack);
 }

@@ -294,6 +294,29 @@ cudaError_t launch_lookback(int L, int modexp, int divide, int threads, const De
     return cudaErrorNotSupported;
 }
 
+// Resident blocks per SM of the latency-mode kernel (512 threads, 16 per
+// thread, CRT route), for one output or two; looked up once per process.
+std::mutex g_occ_mu;
+int g_lat_occ[2][2] = {{-1, -1}, {-1, -1}};  // [rounding exact][both outputs]
+
+int latency_occupancy(bool exact, bool both)
+{
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    int &o = g_lat_occ[exact][both];
+    if (o < 0) {
+        const void *k = exact ? (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_EXACT>
+                              : (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_INT>;
+        const size_t smem = gen_smem_bytes(512, 16, true, both);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 512, smem) != cudaSuccess)
+            b = 0;
+        o = b;
+    }
+    return o;
+}
+
 
 // Tiles of one single-launch call at most (the status array of a scratch
 // slot holds this many); longer draws take the chunked path.
@@ -324,14 +347,32 @@ int generate_single_launch(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *
     const rsaprng_config &cfg = c->cfg;
     if (cfg.lookback == RSAPRNG_LOOKBACK_OFF)
         return RSAPRNG_OK;
-    const GenLaunch g = ctx_launch(c, cfg, 1, d_r != nullptr, d_c != nullptr);
+    GenLaunch g = ctx_launch(c, cfg, 1, d_r != nullptr, d_c != nullptr);
+    if (g.modexp == MODEXP_MONT64 && c->h_params[id].e != c->h_params[id].eq)
+        return fail(RSAPRNG_ERR_ARG, "instance %u has CRT exponents: the 64-bit route cannot "
+                                     "run it", id);
+    // Latency mode. A draw that fits one wave of 512-thread blocks of 16
+    // outputs per thread runs in that shape, on the CRT route with the
+    // integer division. Every block then starts at once and runs the same
+    // phases at the same time, so the phases add up rather than overlap. The
+    // integer division keeps the division phase off the two-lane FP64 pipe,
+    // and the few large tiles keep the look-back short. All shapes and routes
+    // give the same bits; larger draws keep the configured (throughput) shape.
+    if (cfg.lookback != RSAPRNG_LOOKBACK_CONFIGURED) {
+        const bool exact = cfg.rounding == RSAPRNG_ROUND_EXACT;
+        const uint64_t S_lat = 512 * 16;
+        const uint64_t wave = (uint64_t)latency_occupancy(exact, d_r && d_c) * c->sms;
+        if ((N + S_lat - 1) / S_lat <= wave) {
+            g.threads = 512;
+            g.L = 16;
+            g.modexp = MODEXP_CRT32;
+            g.divide = exact ? DIVIDE_EXACT : DIVIDE_INT;
+        }
+    }
     const uint64_t S = (uint64_t)g.threads * g.L;
     const uint64_t ntiles = (N + S - 1) / S;
     if (ntiles > kLbMaxTiles)
         return RSAPRNG_OK;
-    if (g.modexp == MODEXP_MONT64 && c->h_params[id].e != c->h_params[id].eq)
-        return fail(RSAPRNG_ERR_ARG, "instance %u has CRT exponents: the 64-bit route cannot "
-                                     "run it", id);
     uint32_t *err = nullptr;
     int rc = lookback_error_word(c, &err);
     if (rc)

@@ -27,12 +27,11 @@ uint64_t cost_per_number(uint32_t e)
     return (uint64_t)(bl + __builtin_popcount(e) + 6);
 }
 
-// Pieces per resident block that the load balance aims for: the persistent
-// launch hands out items in decreasing cost, and an instance whose work is
-// larger than a block's fair share would otherwise finish alone at the end
-// of the launch. Every extra piece costs a skip-sum pass over the piece
-// before it, so the split is no finer than that.
-constexpr uint64_t kPiecesPerBlock = 1;
+// Pieces per resident block that the load balance aims for (geo.pieces,
+// default 1): the persistent launch hands out items in decreasing cost, and
+// an instance whose work is larger than a block's fair share would otherwise
+// finish alone at the end of the launch. Every extra piece costs a skip-sum
+// pass over the piece before it, so the split is no finer than asked.
 
 // The vector kernel's units (groups of up to G streams side by side) all
 // cost about the same when the streams have one length, so the persistent
@@ -188,7 +187,8 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
         hp.vec_ts = (int)(geo.threads / pack);
         tile = (uint64_t)hp.vec_ts * geo.L;
     }
-    const uint64_t piece_cost = std::max<uint64_t>(1, work / (geo.grid * kPiecesPerBlock * pack));
+    const uint64_t piece_cost =
+        std::max<uint64_t>(1, work / (geo.grid * std::max<uint64_t>(1, geo.pieces) * pack));
     if (tuple > 1 && chunk != ~0ULL)
         chunk = std::max(tile, chunk / tile * tile);
     struct Piece {

@@ -30,9 +30,10 @@ struct HostPlan {
 
 // Shape of the generation launch the pieces are sized for.
 struct PlanGeometry {
-    uint64_t threads;  // threads per block
-    uint64_t L;        // outputs per thread per tile
-    uint64_t grid;     // resident blocks
+    uint64_t threads;     // threads per block
+    uint64_t L;           // outputs per thread per tile
+    uint64_t grid;        // resident blocks
+    uint64_t pieces = 1;  // pieces per resident block the load balance aims for
 };
 
 // Error reporting (defined by the runtime; returns code).

@@ -496,7 +496,13 @@ int rsaprng_autotune(rsaprng_ctx *c, uint64_t nreq, const rsaprng_id *ids, const
             consider(cfg, 0.02f);
         }
     }
-    // Stage 6: the chunk cap of long streams.
+    // Stage 6: pieces per resident block (load balance against skip-sum work).
+    for (int ppb : {2, 4}) {
+        rsaprng_config cfg = best;
+        cfg.pieces_per_block = ppb;
+        consider(cfg, 0.02f);
+    }
+    // Stage 7: the chunk cap of long streams.
     for (uint64_t ch : {1ULL << 16, 1ULL << 17, 1ULL << 19, 1ULL << 20}) {
         if (ch == best.chunk)
             continue;
@@ -573,10 +579,10 @@ int rsaprng_autotune_cache_save(const char *path)
     for (const auto &kv : g_tune_cache) {
         const rsaprng_config &k = kv.second;
         fprintf(f, "%s modexp=%d divide=%d threads=%d numbers=%d blocks_per_sm=%d chunk=%llu "
-                   "streams_per_block=%d unroll=%d rounding=%d\n",
+                   "streams_per_block=%d unroll=%d pieces_per_block=%d rounding=%d\n",
                 kv.first.c_str(), k.modexp, k.divide, k.threads_per_block, k.numbers_per_thread,
                 k.blocks_per_sm, (unsigned long long)k.chunk, k.streams_per_block, k.unroll,
-                k.rounding);
+                k.pieces_per_block, k.rounding);
     }
     const bool ok = fclose(f) == 0;
     return ok ? RSAPRNG_OK : fail(RSAPRNG_ERR_ARG, "autotune cache: write failed");
@@ -591,17 +597,18 @@ int rsaprng_autotune_cache_load(const char *path)
         return fail(RSAPRNG_ERR_ARG, "autotune cache: cannot read %s", path);
     std::map<std::string, rsaprng_config> got;
     char key[256];
-    int modexp, divide, threads, numbers, bps, spb, unroll, rounding;
+    int modexp, divide, threads, numbers, bps, spb, unroll, ppb, rounding;
     unsigned long long chunk;
     int rc = RSAPRNG_OK;
     for (;;) {
         const int n = fscanf(f, "%255s modexp=%d divide=%d threads=%d numbers=%d blocks_per_sm=%d "
-                                "chunk=%llu streams_per_block=%d unroll=%d rounding=%d",
+                                "chunk=%llu streams_per_block=%d unroll=%d pieces_per_block=%d "
+                                "rounding=%d",
                              key, &modexp, &divide, &threads, &numbers, &bps, &chunk, &spb,
-                             &unroll, &rounding);
+                             &unroll, &ppb, &rounding);
         if (n == EOF)
             break;
-        if (n != 10) {
+        if (n != 11) {
             rc = fail(RSAPRNG_ERR_ARG, "autotune cache: malformed line in %s", path);
             break;
         }
@@ -615,6 +622,7 @@ int rsaprng_autotune_cache_load(const char *path)
         k.chunk = chunk;
         k.streams_per_block = spb;
         k.unroll = unroll;
+        k.pieces_per_block = ppb;
         k.rounding = rounding;
         got[key] = k;
     }

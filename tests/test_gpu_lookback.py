@@ -61,7 +61,8 @@ def _draw(ctx, i, n, both=True):
     dict(modexp=R.MODEXP_MONT64, numbers_per_thread=8, divide=R.DIVIDE_INT),
 ])
 def test_single_launch_sizes_against_oracle(O, cfg):
-    ctx = R.Context(4, **cfg)
+    """The configured shapes (the latency shape switched off)."""
+    ctx = R.Context(4, lookback=R.LOOKBACK_CONFIGURED, **cfg)
     i, (p, q, e, m0) = _instance(ctx, O, 71)
     k = ctx.config()
     S = k["threads_per_block"] * min(k["numbers_per_thread"],
@@ -82,10 +83,32 @@ def test_single_launch_sizes_against_oracle(O, cfg):
     assert ctx.device_status() == 0
 
 
+@pytest.mark.parametrize("rounding", [0, 2])
+def test_latency_shape_sizes_against_oracle(O, rounding):
+    """The latency shape (512 x 16, CRT, integer division) for draws that fit one wave,
+    around its tiles and the wave's end, then the configured shape beyond it."""
+    ctx = R.Context(4, rounding=rounding)
+    i, (p, q, e, m0) = _instance(ctx, O, 74)
+    S = 512 * 16
+    m, s = m0, 1
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    for n in (1, S - 1, S, S + 1, 1_000_000, sm * S, sm * S + 1):
+        launches = ctx.launches
+        c, r = _draw(ctx, i, n)
+        assert ctx.launches - launches == 1
+        want_c, want_r, m, s = O.generate(p, q, e, m, s, n, a=A)
+        if rounding == 2:
+            want_r = O.unit_exact_many(want_c, p * q)
+        assert (c == want_c).all(), f"n={n}: c differs"
+        assert (r.view(np.uint64) == want_r.view(np.uint64)).all(), f"n={n}: r differs"
+        assert ctx.get_state(i) == (m, s)
+    assert ctx.device_status() == 0
+
+
 def test_single_launch_limit_and_chunked_path_agree(O):
     """At 4096 tiles the call is one launch; one more output takes the chunked path; with
     the single launch switched off the same draws give the same bits."""
-    a = R.Context(4)
+    a = R.Context(4, lookback=R.LOOKBACK_CONFIGURED)
     b = R.Context(4, lookback=R.LOOKBACK_OFF)
     ia, prm = _instance(a, O, 72, R.E_SMALLEST, 3, 3)
     ib, _ = _instance(b, O, 72, R.E_SMALLEST, 3, 3)

@@ -120,6 +120,7 @@ def test_routes_and_tilings_ragged(O, modexp, divide, threads, L):
     dict(unroll=8), dict(unroll=8, divide=R.DIVIDE_HYBRID), dict(unroll=8, divide=R.DIVIDE_INT),
     dict(unroll=4, numbers_per_thread=8), dict(unroll=2),  # the last: no variant, all at once
     dict(unroll=8, streams_per_block=2, chunk=4096),
+    dict(pieces_per_block=4), dict(pieces_per_block=3, streams_per_block=2),
 ])
 def test_packed_streams_and_chain_passes(O, cfg):
     """The autotuner's knobs: several streams per block (segments of whole warps, pieces of
@@ -445,7 +446,7 @@ def test_autotune_cache(O, tmp_path):
     cfg2, hit2 = ctx2.autotune_cached(ids2, counts, reps=1)
     assert hit2
     knobs = ("modexp", "divide", "threads_per_block", "numbers_per_thread", "blocks_per_sm",
-             "chunk", "streams_per_block", "unroll")
+             "chunk", "streams_per_block", "unroll", "pieces_per_block")
     assert {k: cfg1[k] for k in knobs} == {k: cfg2[k] for k in knobs}
     path = str(tmp_path / "tune.txt")
     assert L.rsaprng_autotune_cache_save(path.encode()) == 0

@@ -113,9 +113,11 @@ def test_autotune_cache_file_round_trip(R, tmp_path):
     L = R._lib.load()
     L.rsaprng_autotune_cache_clear()
     lines = ["sm103-x152/req2^10-mean2^14-max2^23/rounding0/e6 modexp=1 divide=4 threads=128 "
-             "numbers=16 blocks_per_sm=0 chunk=262144 streams_per_block=2 unroll=8 rounding=0",
+             "numbers=16 blocks_per_sm=0 chunk=262144 streams_per_block=2 unroll=8 pieces_per_block=1 "
+             "rounding=0",
              "sm103-x152/req2^0-mean2^19-max2^19/rounding0/e4 modexp=1 divide=3 threads=256 "
-             "numbers=8 blocks_per_sm=4 chunk=65536 streams_per_block=1 unroll=0 rounding=0"]
+             "numbers=8 blocks_per_sm=4 chunk=65536 streams_per_block=1 unroll=0 pieces_per_block=4 "
+             "rounding=0"]
     src = tmp_path / "in.txt"
     src.write_text("\n".join(lines) + "\n")
     assert L.rsaprng_autotune_cache_load(str(src).encode()) == 0
