@@ -66,8 +66,9 @@ def parse_args(argv=None):
                     help="override numbers per instance (small profiling runs only)")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--per-thread", type=int, default=0)
-    ap.add_argument("--pieces-per-block", type=int, default=0,
-                    help="load-balance pieces per resident block (0: the default, 1)")
+    ap.add_argument("--pieces-per-block", type=int, default=4,
+                    help="load-balance pieces per resident block of the bulk plan (measured "
+                         "best on the bulk workload: 4)")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="cap on resident generation blocks per SM (0: occupancy limit)")
     ap.add_argument("--modexp", type=int, default=0)

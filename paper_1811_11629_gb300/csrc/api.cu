@@ -165,7 +165,7 @@ GenLaunch ctx_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nitems,
 }
 
 static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nvecs, bool want_r,
-                            bool want_c);
+                            bool want_c, bool packed);
 
 int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const rsaprng_id *ids,
                const uint64_t *counts, const uint64_t *offsets, uint64_t chunk, HostPlan &hp,
@@ -177,8 +177,9 @@ int build_plan(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nreq, const r
     const uint64_t pack = allow_pack && stride == 1 && tuple == 1 && cfg.streams_per_block > 1
                               ? (uint64_t)cfg.streams_per_block
                               : 1;
-    const GenLaunch full = (stride > 1 || pack > 1) ? vec_launch(c, cfg, ~0ULL, true, false)
-                                                    : ctx_launch(c, cfg, ~0ULL, true, false);
+    const GenLaunch full = (stride > 1 || pack > 1)
+                               ? vec_launch(c, cfg, ~0ULL, true, false, pack > 1)
+                               : ctx_launch(c, cfg, ~0ULL, true, false);
     const PlanGeometry geo{(uint64_t)full.threads, (uint64_t)full.L, (uint64_t)full.grid,
                            (uint64_t)std::max(1, cfg.pieces_per_block)};
     return build_plan_core(c->h_params.data(), c->count, cfg.modexp, geo, nreq, ids, counts,
@@ -272,10 +273,11 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
 
 // Launch shape of the vector kernel (interleaved order) for cfg.
 static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t nvecs, bool want_r,
-                            bool want_c)
+                            bool want_c, bool packed)
 {
     GenLaunch g = ctx_launch(c, cfg, nvecs, want_r, want_c);
     g.L = vec_numbers_per_thread(g.L, g.modexp, g.threads);
+    g.stride = packed ? 1 : 2;  // selects the packed or the interleaved kernel
     int occ = vec_blocks_per_sm(g, vec_smem_bytes(g.threads, g.L, want_r, want_c));
     if (occ < 1)
         occ = 1;
@@ -313,7 +315,7 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
     GenLaunch g{};
     if (dp.nitems) {
         g = hist  ? hist_launch(c, cfg, dp.nitems)
-            : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr)
+            : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr, dp.stride == 1)
                   : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
         g.stride = dp.stride;
         g.pdl = dp.nchunks > 0;

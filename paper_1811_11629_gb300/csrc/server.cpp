@@ -310,12 +310,16 @@ bool launch_iteration(rsaprng_server *S, Slot &sl)
     chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(S->ctx->cfg.chunk, tile));
     HostPlan hp;
     cudaEventRecord(sl.start, sl.stream);
-    int rc = build_plan(S->ctx, S->ctx->cfg, ids.size(), ids.data(), counts.data(), offs.data(),
+    // The iteration sizes its pieces itself (the chunk above); the load-balance
+    // split for long launches would only add skip-sum work to short ones.
+    rsaprng_config cfg = S->ctx->cfg;
+    cfg.pieces_per_block = 1;
+    int rc = build_plan(S->ctx, cfg, ids.size(), ids.data(), counts.data(), offs.data(),
                         chunk, hp, 1, 1, true);
     if (rc == RSAPRNG_OK)
         rc = upload_plan(S->ctx, hp, sl.plan, sl.stream);
     if (rc == RSAPRNG_OK)
-        rc = launch_plan(S->ctx, S->ctx->cfg, sl.plan, S->d_arena, nullptr, sl.stream, nullptr,
+        rc = launch_plan(S->ctx, cfg, sl.plan, S->d_arena, nullptr, sl.stream, nullptr,
                          nullptr, true);
     cudaEventRecord(sl.done, sl.stream);
     sl.t_launch = now_s();

@@ -33,8 +33,10 @@ using tile::sidx;
 using tile::to_unit;
 
 // TB > 0: the tuned instance for blocks of exactly TB threads, bounded to
-// five resident blocks per SM.
-template <int L, int MODEXP, int DIV, int TB>
+// five resident blocks per SM. PACKED: unrelated streams side by side (stride
+// 1, per-segment lengths, segments of whole warps); otherwise the interleaved
+// order (equal lengths, segments within a warp).
+template <int L, int MODEXP, int DIV, int TB, bool PACKED>
 __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     k_generate_vec(DeviceTables tab, const WorkItem *__restrict__ items,
                    const VecGroup *__restrict__ vecs, uint32_t nvecs, uint32_t *ticket,
@@ -85,18 +87,21 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
         // This segment's length, and the group's (its first item is the
         // longest); in the interleaved order they are all equal.
         const u64 count = W.count;
-        const u64 gcount = items[V.first].count;
+        const u64 gcount = PACKED ? items[V.first].count : count;
         const u64 o0 = items[V.first].out_off;
         for (u64 base = 0; base < gcount; base += K) {
-            const u64 left = count > base ? count - base : 0;
+            const u64 left = !PACKED || count > base ? count - base : 0;
             const int tile_n = left < (u64)K ? (int)left : K;
             const int nvalid = !on ? 0 : (tile_n - my0 < 0 ? 0 : (tile_n - my0 > L ? L : tile_n - my0));
             u64 c[L], total;
             tile::tile_ciphertexts_scan<L, MODEXP>(
                 tab, W, P, m, s_thr, left, my0, nvalid,
                 [&](u64 x, u64 nn, u64 &tot) {
-                    return TS <= 32 ? tile::segment_exscan_mod(x, nn, TS, tot)
-                                    : tile::segment_exscan_mod_warps(x, nn, TS, sh_scan, tot);
+                    if constexpr (PACKED) {
+                        if (TS > 32)
+                            return tile::segment_exscan_mod_warps(x, nn, TS, sh_scan, tot);
+                    }
+                    return tile::segment_exscan_mod(x, nn, TS, tot);
                 },
                 c, total);
             // staged by instance: slot seg K + position (padded every 16)
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
                     st_c[sidx(row0 + j)] = c[j];
             }
             __syncthreads();
-            if (stride == 1) {
+            if constexpr (PACKED) {
                 // Packed streams: each segment's run is contiguous at its own
                 // offset, written by its TS threads.
                 if (on) {
@@ -170,37 +175,44 @@ constexpr bool vec_tuned()
     return L == kVecTunedL && MODEXP == MODEXP_CRT32;
 }
 
-template <int L, int MODEXP, int DIV>
+template <int L, int MODEXP, int DIV, bool PACKED>
 auto vec_kernel(int threads)
 {
     if constexpr (vec_tuned<L, MODEXP>())
         if (threads == kVecTunedThreads)
-            return k_generate_vec<L, MODEXP, DIV, kVecTunedThreads>;
-    return k_generate_vec<L, MODEXP, DIV, 0>;
+            return k_generate_vec<L, MODEXP, DIV, kVecTunedThreads, PACKED>;
+    return k_generate_vec<L, MODEXP, DIV, 0, PACKED>;
+}
+
+template <int L, int MODEXP, int DIV>
+const void *vec_kernel_any(int threads, bool packed)
+{
+    return packed ? (const void *)vec_kernel<L, MODEXP, DIV, true>(threads)
+                  : (const void *)vec_kernel<L, MODEXP, DIV, false>(threads);
 }
 
 // Every division route gives the same bits, so the vector kernel is
 // instantiated for the integer and reciprocal routes (the others map to the
 // reciprocal one) and for the exact-rational reading.
 template <int DIV>
-const void *vec_kernel_ptr_d(int L, int modexp, int threads)
+const void *vec_kernel_ptr_d(int L, int modexp, int threads, bool packed)
 {
     if (modexp == MODEXP_CRT32) {
         if (L == 16)
-            return (const void *)vec_kernel<16, MODEXP_CRT32, DIV>(threads);
+            return vec_kernel_any<16, MODEXP_CRT32, DIV>(threads, packed);
         if (L == 8)
-            return (const void *)vec_kernel<8, MODEXP_CRT32, DIV>(threads);
+            return vec_kernel_any<8, MODEXP_CRT32, DIV>(threads, packed);
         if (L == 4)
-            return (const void *)vec_kernel<4, MODEXP_CRT32, DIV>(threads);
+            return vec_kernel_any<4, MODEXP_CRT32, DIV>(threads, packed);
         if (L == 2)
-            return (const void *)vec_kernel<2, MODEXP_CRT32, DIV>(threads);
+            return vec_kernel_any<2, MODEXP_CRT32, DIV>(threads, packed);
     } else {
         if (L == 8)
-            return (const void *)vec_kernel<8, MODEXP_MONT64, DIV>(threads);
+            return vec_kernel_any<8, MODEXP_MONT64, DIV>(threads, packed);
         if (L == 4)
-            return (const void *)vec_kernel<4, MODEXP_MONT64, DIV>(threads);
+            return vec_kernel_any<4, MODEXP_MONT64, DIV>(threads, packed);
         if (L == 2)
-            return (const void *)vec_kernel<2, MODEXP_MONT64, DIV>(threads);
+            return vec_kernel_any<2, MODEXP_MONT64, DIV>(threads, packed);
     }
     return nullptr;
 }
@@ -212,20 +224,21 @@ int vec_div(int divide)
 
 const void *vec_kernel_ptr(const GenLaunch &g)
 {
+    const bool packed = g.stride == 1;
     switch (vec_div(g.divide)) {
-    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp, g.threads);
-    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp, g.threads);
-    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp, g.threads);
+    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp, g.threads, packed);
+    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp, g.threads, packed);
+    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp, g.threads, packed);
     }
 }
 
-template <int L, int MODEXP, int DIV>
-cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+template <int L, int MODEXP, int DIV, bool PACKED>
+cudaError_t launch_vec_p(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                          const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
                          uint64_t *out_c, int TS, cudaStream_t stream)
 {
     const size_t smem = vec_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = vec_kernel<L, MODEXP, DIV>(g.threads);
+    auto kern = vec_kernel<L, MODEXP, DIV, PACKED>(g.threads);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -234,6 +247,18 @@ cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
     }
     return launch_kernel(kern, g.grid, g.threads, smem, stream, g.pdl, t, items, vecs, nvecs,
                          g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride, TS);
+}
+
+template <int L, int MODEXP, int DIV>
+cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+                         const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
+                         uint64_t *out_c, int TS, cudaStream_t stream)
+{
+    if (g.stride == 1)  // packed streams
+        return launch_vec_p<L, MODEXP, DIV, true>(g, t, items, vecs, nvecs, ticket, out_r, out_c,
+                                                  TS, stream);
+    return launch_vec_p<L, MODEXP, DIV, false>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+                                               stream);
 }
 
 template <int DIV>
