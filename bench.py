@@ -609,12 +609,19 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     for f in loads:
         rate = f * cap_rate
         arr = workload.poisson_arrivals(63 + int(f * 100), nreq, rate)
-        srv.replay(pick, cnt, arr, timeout_s=300)
-        st = srv.stats()
+        # three replays of the same trace; the one with the median p99 is reported
+        runs = []
+        for _ in range(3):
+            srv.replay(pick, cnt, arr, timeout_s=300)
+            runs.append(srv.stats())
+        runs.sort(key=lambda s: s["p99_ms"])
+        st = runs[1]
         points.append({"load": f, "offered_req_per_s": round(rate, 1),
                        "throughput": round(st["numbers_done"] / st["wall_s"] / 1e9, 3),
                        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                       "iterations": st["iterations"]})
+                       "p99_ms_of_replays": [round(s["p99_ms"], 3) for s in runs],
+                       "iterations": st["iterations"],
+                       "overlapped_iterations": st["overlapped_iterations"]})
     es = [ctx.params(int(i))[2] for i in pick[:200]]
     mean_slots = float(np.mean([imad_slots_per_number(int(e)) for e in es]))
     divide = ctx.config()["divide"]
