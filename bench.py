@@ -69,6 +69,10 @@ def parse_args(argv=None):
     ap.add_argument("--pieces-per-block", type=int, default=4,
                     help="load-balance pieces per resident block of the bulk plan (measured "
                          "best on the bulk workload: 4)")
+    ap.add_argument("--unroll", type=int, default=0,
+                    help="exponentiation chains per pass (0: all of a thread's numbers)")
+    ap.add_argument("--streams-per-block", type=int, default=0,
+                    help="streams side by side in a block (0: one)")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="cap on resident generation blocks per SM (0: occupancy limit)")
     ap.add_argument("--modexp", type=int, default=0)
@@ -661,7 +665,9 @@ def run_ours(args) -> int:
                                ("numbers_per_thread", args.per_thread),
                                ("modexp", args.modexp), ("divide", args.divide),
                                ("blocks_per_sm", args.blocks_per_sm),
-                               ("pieces_per_block", args.pieces_per_block)) if y}
+                               ("pieces_per_block", args.pieces_per_block),
+                               ("unroll", args.unroll),
+                               ("streams_per_block", args.streams_per_block)) if y}
     ctx = R.Context(k, device=dist.local_rank, chunk=n, **knobs)
     first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
