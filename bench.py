@@ -55,6 +55,8 @@ def parse_args(argv=None):
                     help="skip the plain / batched / served forms")
     ap.add_argument("--forms", default=",".join(FORMS),
                     help="comma-separated subset of the forms to run (profiling runs)")
+    ap.add_argument("--batched-instances", type=int, default=0,
+                    help="instances of the batched form (small profiling runs only)")
     ap.add_argument("--parents", type=int, default=1024,
                     help="split parents of the interleaved form (small profiling runs only)")
     ap.add_argument("--tune", action="store_true", help="autotune the tiling before timing")
@@ -422,11 +424,12 @@ def form_plain(R, torch, device, pk, rank) -> dict:
     return out
 
 
-def form_batched(R, torch, device, pk, rank) -> dict:
+def form_batched(R, torch, device, pk, rank, k=0) -> dict:
     """Batched uneven: 1e5 instances, lognormal lengths (~2^32 outputs, f64), one plan in a
-    CUDA graph after autotuning on the whole workload (or a tuning-cache hit)."""
+    CUDA graph after autotuning on the whole workload (or a tuning-cache hit). k overrides
+    the instance count (the first k of the workload; small profiling runs)."""
     cfg = workload.CONFIGS["batched_1e5_lognormal"]
-    k = cfg["instances"]
+    k = k or cfg["instances"]
     lens = workload.lognormal_lengths(cfg["master"] + 1000 * rank, k)
     ctx = R.Context(k, device=device)
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
@@ -794,7 +797,7 @@ def run_ours(args) -> int:
         lr, rk = dist.local_rank, dist.rank
         runs = (("plain_1x1e6", "plain", lambda: form_plain(R, torch, lr, pk, rk)),
                 ("batched_1e5_lognormal", "batched",
-                 lambda: form_batched(R, torch, lr, pk, rk)),
+                 lambda: form_batched(R, torch, lr, pk, rk, args.batched_instances)),
                 ("serving_1e6", "served", lambda: form_served(R, torch, lr, pk, rk)),
                 ("fused_histogram_bulk", "fused",
                  lambda: form_fused(R, torch, lr, pk, rk, args.instances, args.count)),

@@ -79,6 +79,12 @@ def test_random_configurations_and_entry_points(O, seed):
     cfg = dict(modexp=modexp, divide=rng.choice([1, 2, 3, 4]), threads_per_block=T,
                numbers_per_thread=L, chunk=rng.choice([0, 1 << 12, 1 << 14, 1 << 16]),
                rounding=R._lib.ROUND_EXACT if exact else R._lib.ROUND_PAPER)
+    # the autotuner's knobs (each bit-identical to the default)
+    if rng.random() < 0.3 and T // 2 >= 32:
+        cfg["streams_per_block"] = 2
+    if rng.random() < 0.3:
+        cfg["unroll"] = max(1, L // 2)
+    cfg["pieces_per_block"] = rng.choice([0, 1, 4])
     cfg = {k: v for k, v in cfg.items() if v}
     ctx = R.Context(32, **cfg)
     insts = [Inst(O, ctx, rng, crt_ok=modexp == R.MODEXP_CRT32) for _ in range(6)]
@@ -132,6 +138,20 @@ def test_random_configurations_and_entry_points(O, seed):
     for g, i in enumerate(sel):
         _, r = insts[i].take(O, N, exact)
         assert (bits(got[g::len(sel)]) == bits(r)).all()
+
+    # the direct one-instance call: one launch (latency or configured shape) or the
+    # chunked path
+    ctx.configure(lookback=rng.choice([R.LOOKBACK_AUTO, R.LOOKBACK_CONFIGURED, R.LOOKBACK_OFF]))
+    i = rng.randrange(len(insts))
+    N = rng.choice([1, rng.randrange(2, 70000), rng.randrange(70000, 1_500_000)])
+    dc = torch.empty(N, dtype=torch.int64, device="cuda")
+    dr = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.generate_both(insts[i].id, N, dc, dr)
+    torch.cuda.synchronize()
+    c, r = insts[i].take(O, N, exact)
+    np.testing.assert_array_equal(dc.cpu().numpy().view(np.uint64), c)
+    assert (bits(dr.cpu().numpy()) == bits(r)).all()
+    assert ctx.device_status() == 0
 
     # every state where the oracle says it is
     for inst in insts:
