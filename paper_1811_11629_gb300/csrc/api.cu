@@ -276,6 +276,7 @@ static GenLaunch vec_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t 
                             bool want_c, bool packed)
 {
     GenLaunch g = ctx_launch(c, cfg, nvecs, want_r, want_c);
+    g.L_wide = g.L;
     g.L = vec_numbers_per_thread(g.L, g.modexp, g.threads);
     g.stride = packed ? 1 : 2;  // selects the packed or the interleaved kernel
     int occ = vec_blocks_per_sm(g, vec_smem_bytes(g.threads, g.L, want_r, want_c));

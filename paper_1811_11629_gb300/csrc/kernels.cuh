@@ -43,6 +43,8 @@ struct GenLaunch {
     uint64_t stride; // element distance between consecutive outputs of a work item
     bool pdl = false;  // launch as a programmatic dependent of the start-state scan
     int unroll = 0;    // 0 or >= L: all L chains at once; else passes of this many
+    int L_wide = 0;    // vector kernel: the configured numbers per thread, which
+                       // whole-warp segments may run instead of L
 };
 
 // Launches kern; with pdl as a programmatic dependent of the kernel before it

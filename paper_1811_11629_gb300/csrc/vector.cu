@@ -33,10 +33,14 @@ using tile::sidx;
 using tile::to_unit;
 
 // TB > 0: the tuned instance for blocks of exactly TB threads, bounded to
-// five resident blocks per SM. PACKED: unrelated streams side by side (stride
-// 1, per-segment lengths, segments of whole warps); otherwise the interleaved
-// order (equal lengths, segments within a warp).
-template <int L, int MODEXP, int DIV, int TB, bool PACKED>
+// five resident blocks per SM. MODE 0: the interleaved order with segments
+// inside a warp (TS < 32); MODE 1: the interleaved order with segments of
+// whole warps (TS >= 32); MODE 2: unrelated streams side by side (stride 1,
+// per-segment lengths, segments of whole warps). With whole-warp segments
+// the segment index comes from lane 0, so the compiler knows it is the same
+// across the warp and keeps the instance's parameters in uniform registers
+// (the interleaved 16-per-thread kernel: 96 registers instead of 128).
+template <int L, int MODEXP, int DIV, int TB, int MODE>
 __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     k_generate_vec(DeviceTables tab, const WorkItem *__restrict__ items,
                    const VecGroup *__restrict__ vecs, uint32_t nvecs, uint32_t *ticket,
@@ -48,7 +52,9 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     __shared__ uint32_t sh_item;
     const int T = TB ? TB : (int)blockDim.x, t = threadIdx.x;
     const int tsh = __ffs(TS) - 1, G = T >> tsh, gsh = __ffs(G) - 1;  // both powers of two
-    const int seg = t >> tsh, lt = t & (TS - 1);
+    constexpr bool PACKED = MODE == 2;
+    const int seg = MODE >= 1 ? __shfl_sync(0xFFFFFFFFu, t >> tsh, 0) : t >> tsh;
+    const int lt = t & (TS - 1);
     const int wcol = t & (G - 1), wk0 = t >> gsh;  // this thread's column and first row in stores
     const int K = TS * L;  // positions of each instance per tile
     const int S = K * G;   // = T L outputs per tile
@@ -161,58 +167,80 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     }
 }
 
-// The tuned tile of the vector kernel: 8 numbers per thread in blocks of
-// 128 threads on the CRT route. Unlike the instance-major kernel, every
-// thread holds its own instance's parameters, and 16 numbers per thread no
-// longer fit the register budget of five resident blocks per SM (the
-// compiler spills); 8 do, and five blocks of 8 outrun four of 16.
+// The tuned tiles of the vector kernel, in blocks of 128 threads on the CRT
+// route bounded to five resident blocks per SM: 8 numbers per thread always,
+// and 16 when segments are whole warps. Segments inside a warp make every
+// thread hold its own instance's parameters, and 16 numbers per thread then
+// no longer fit the register budget of five blocks (the compiler spills).
 constexpr int kVecTunedThreads = 128;
 constexpr int kVecTunedL = 8;
+constexpr int kVecWideL = 16;
 
-template <int L, int MODEXP>
+template <int L, int MODEXP, int MODE>
 constexpr bool vec_tuned()
 {
-    return L == kVecTunedL && MODEXP == MODEXP_CRT32;
+    return MODEXP == MODEXP_CRT32 && (L == kVecTunedL || (L == kVecWideL && MODE >= 1));
 }
 
-template <int L, int MODEXP, int DIV, bool PACKED>
+template <int L, int MODEXP, int DIV, int MODE>
 auto vec_kernel(int threads)
 {
-    if constexpr (vec_tuned<L, MODEXP>())
+    if constexpr (vec_tuned<L, MODEXP, MODE>())
         if (threads == kVecTunedThreads)
-            return k_generate_vec<L, MODEXP, DIV, kVecTunedThreads, PACKED>;
-    return k_generate_vec<L, MODEXP, DIV, 0, PACKED>;
+            return k_generate_vec<L, MODEXP, DIV, kVecTunedThreads, MODE>;
+    return k_generate_vec<L, MODEXP, DIV, 0, MODE>;
+}
+
+// Whole-warp interleaved kernels (MODE 1) exist for the tilings that the
+// vector call runs (16 and 8 per thread on the CRT route, 8 on the 64-bit
+// route); elsewhere MODE 0 serves every segment width.
+template <int L, int MODEXP>
+constexpr bool has_warp_mode()
+{
+    return (MODEXP == MODEXP_CRT32 && (L == 16 || L == 8)) || (MODEXP == MODEXP_MONT64 && L == 8);
+}
+
+template <int L, int MODEXP>
+int effective_mode(int mode)
+{
+    return mode == 1 && !has_warp_mode<L, MODEXP>() ? 0 : mode;
 }
 
 template <int L, int MODEXP, int DIV>
-const void *vec_kernel_any(int threads, bool packed)
+const void *vec_kernel_any(int threads, int mode)
 {
-    return packed ? (const void *)vec_kernel<L, MODEXP, DIV, true>(threads)
-                  : (const void *)vec_kernel<L, MODEXP, DIV, false>(threads);
+    switch (effective_mode<L, MODEXP>(mode)) {
+    case 2: return (const void *)vec_kernel<L, MODEXP, DIV, 2>(threads);
+    case 1:
+        if constexpr (has_warp_mode<L, MODEXP>())
+            return (const void *)vec_kernel<L, MODEXP, DIV, 1>(threads);
+        return nullptr;
+    default: return (const void *)vec_kernel<L, MODEXP, DIV, 0>(threads);
+    }
 }
 
 // Every division route gives the same bits, so the vector kernel is
 // instantiated for the integer and reciprocal routes (the others map to the
 // reciprocal one) and for the exact-rational reading.
 template <int DIV>
-const void *vec_kernel_ptr_d(int L, int modexp, int threads, bool packed)
+const void *vec_kernel_ptr_d(int L, int modexp, int threads, int mode)
 {
     if (modexp == MODEXP_CRT32) {
         if (L == 16)
-            return vec_kernel_any<16, MODEXP_CRT32, DIV>(threads, packed);
+            return vec_kernel_any<16, MODEXP_CRT32, DIV>(threads, mode);
         if (L == 8)
-            return vec_kernel_any<8, MODEXP_CRT32, DIV>(threads, packed);
+            return vec_kernel_any<8, MODEXP_CRT32, DIV>(threads, mode);
         if (L == 4)
-            return vec_kernel_any<4, MODEXP_CRT32, DIV>(threads, packed);
+            return vec_kernel_any<4, MODEXP_CRT32, DIV>(threads, mode);
         if (L == 2)
-            return vec_kernel_any<2, MODEXP_CRT32, DIV>(threads, packed);
+            return vec_kernel_any<2, MODEXP_CRT32, DIV>(threads, mode);
     } else {
         if (L == 8)
-            return vec_kernel_any<8, MODEXP_MONT64, DIV>(threads, packed);
+            return vec_kernel_any<8, MODEXP_MONT64, DIV>(threads, mode);
         if (L == 4)
-            return vec_kernel_any<4, MODEXP_MONT64, DIV>(threads, packed);
+            return vec_kernel_any<4, MODEXP_MONT64, DIV>(threads, mode);
         if (L == 2)
-            return vec_kernel_any<2, MODEXP_MONT64, DIV>(threads, packed);
+            return vec_kernel_any<2, MODEXP_MONT64, DIV>(threads, mode);
     }
     return nullptr;
 }
@@ -222,23 +250,29 @@ int vec_div(int divide)
     return divide == DIVIDE_EXACT ? DIVIDE_EXACT : divide == DIVIDE_INT ? DIVIDE_INT : DIVIDE_RECIP;
 }
 
-const void *vec_kernel_ptr(const GenLaunch &g)
+// The launch mode for segments of TS threads (0: unknown width, taken as
+// inside a warp).
+int vec_mode(const GenLaunch &g, int TS)
 {
-    const bool packed = g.stride == 1;
+    return g.stride == 1 ? 2 : (TS >= 32 ? 1 : 0);
+}
+
+const void *vec_kernel_ptr(const GenLaunch &g, int mode)
+{
     switch (vec_div(g.divide)) {
-    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp, g.threads, packed);
-    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp, g.threads, packed);
-    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp, g.threads, packed);
+    case DIVIDE_EXACT: return vec_kernel_ptr_d<DIVIDE_EXACT>(g.L, g.modexp, g.threads, mode);
+    case DIVIDE_INT: return vec_kernel_ptr_d<DIVIDE_INT>(g.L, g.modexp, g.threads, mode);
+    default: return vec_kernel_ptr_d<DIVIDE_RECIP>(g.L, g.modexp, g.threads, mode);
     }
 }
 
-template <int L, int MODEXP, int DIV, bool PACKED>
+template <int L, int MODEXP, int DIV, int MODE>
 cudaError_t launch_vec_p(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
                          const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
                          uint64_t *out_c, int TS, cudaStream_t stream)
 {
     const size_t smem = vec_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = vec_kernel<L, MODEXP, DIV, PACKED>(g.threads);
+    auto kern = vec_kernel<L, MODEXP, DIV, MODE>(g.threads);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -254,11 +288,19 @@ cudaError_t launch_vec_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
                          const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket, double *out_r,
                          uint64_t *out_c, int TS, cudaStream_t stream)
 {
-    if (g.stride == 1)  // packed streams
-        return launch_vec_p<L, MODEXP, DIV, true>(g, t, items, vecs, nvecs, ticket, out_r, out_c,
-                                                  TS, stream);
-    return launch_vec_p<L, MODEXP, DIV, false>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+    switch (effective_mode<L, MODEXP>(vec_mode(g, TS))) {
+    case 2:
+        return launch_vec_p<L, MODEXP, DIV, 2>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
                                                stream);
+    case 1:
+        if constexpr (has_warp_mode<L, MODEXP>())
+            return launch_vec_p<L, MODEXP, DIV, 1>(g, t, items, vecs, nvecs, ticket, out_r, out_c,
+                                                   TS, stream);
+        return cudaErrorInvalidValue;
+    default:
+        return launch_vec_p<L, MODEXP, DIV, 0>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
+                                               stream);
+    }
 }
 
 template <int DIV>
@@ -294,10 +336,16 @@ size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
     return gen_smem_bytes(threads, L, want_r, want_c);  // the same padded slots
 }
 
-cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const WorkItem *items,
+cudaError_t launch_generate_vec(const GenLaunch &g0, const DeviceTables &t, const WorkItem *items,
                                 const VecGroup *vecs, uint32_t nvecs, uint32_t *ticket,
                                 double *out_r, uint64_t *out_c, int TS, cudaStream_t stream)
 {
+    // Whole-warp segments take the configured 16 per thread where the plan
+    // was cut in tiles of 8 (pieces need not be whole tiles of the kernel).
+    GenLaunch g = g0;
+    if (vec_mode(g, TS) >= 1 && g.modexp == MODEXP_CRT32 && g.threads == kVecTunedThreads &&
+        g.L == kVecTunedL && g.L_wide == kVecWideL)
+        g.L = kVecWideL;
     switch (vec_div(g.divide)) {
     case DIVIDE_EXACT:
         return launch_vec_d<DIVIDE_EXACT>(g, t, items, vecs, nvecs, ticket, out_r, out_c, TS,
@@ -313,7 +361,7 @@ cudaError_t launch_generate_vec(const GenLaunch &g, const DeviceTables &t, const
 
 int vec_blocks_per_sm(const GenLaunch &g, size_t smem)
 {
-    const void *k = vec_kernel_ptr(g);
+    const void *k = vec_kernel_ptr(g, g.stride == 1 ? 2 : 0);
     if (!k)
         return 0;
     if (smem > 48 * 1024)
