@@ -266,8 +266,13 @@ def test_unit_step_random_and_edges(O, divide):
         cs = [rng.integers(0, n, 400000, dtype=np.uint64)]
         cs.append(np.uint64(n) - rng.integers(1, 1 << 14, 20000, dtype=np.uint64))
         cs.append(rng.integers(0, 1 << 54, 20000, dtype=np.uint64))
+        cs.append(rng.integers(0, 1 << 32, 20000, dtype=np.uint64))  # high word zero
+        # every bit length, random significands (the conversion's normalisation shift)
+        cs += [rng.integers(1 << (b - 1), 1 << b, 200, dtype=np.uint64)
+               for b in range(1, n.bit_length())]
         edge = [0, 1, 2, (1 << 53) - 1, 1 << 53, (1 << 53) + 1, (1 << 62) - 1, 1 << 62, n - 1,
-                n - 2, n >> 1]
+                n - 2, n >> 1, (1 << 32) - 1, 1 << 32, (1 << 32) + 1]
+        edge += [(1 << b) + d for b in range(1, n.bit_length() - 1) for d in (-1, 0, 1)]
         # values whose conversion to double is an exact tie (ties to even), all bit lengths
         for bl in range(54, n.bit_length() + 1):
             for mant in rng.integers(1 << 52, 1 << 53, 64):
