@@ -261,6 +261,7 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     dp.nchunks = (uint32_t)hp.chunks.size();
     dp.ngroups = (uint32_t)hp.groups.size();
     dp.numbers = hp.numbers;
+    dp.extent = hp.extent;
     dp.stride = hp.stride;
     dp.nvecs = (uint32_t)hp.vecs.size();
     dp.vec_ts = hp.vec_ts;
@@ -319,6 +320,7 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
             : vec ? vec_launch(c, cfg, dp.nvecs, d_r != nullptr, d_c != nullptr, dp.stride == 1)
                   : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
         g.stride = dp.stride;
+        g.out_extent = dp.extent;
         g.pdl = dp.nchunks > 0;
         dp.last = g;
         // A persistent launch's ticket is reset before the pre-pass, so that the

@@ -30,6 +30,7 @@ struct DevPlan {
     uint64_t *chunk_s = nullptr;
     uint32_t nitems = 0, nchunks = 0, ngroups = 0;
     uint64_t numbers = 0;
+    uint64_t extent = 0;  // one past the last output element the plan writes
     uint64_t stride = 1;
     VecGroup *vecs = nullptr;
     uint32_t nvecs = 0;

@@ -16,6 +16,7 @@
 // scan per instance give every chunk its start state, so no block ever waits
 // for another (no inter-block spin).
 #include <cstdio>
+#include <cstring>
 
 #include "device_math.cuh"
 #include "kernels.cuh"
@@ -38,7 +39,6 @@ using tile::pdl_trigger;
 using tile::pdl_wait;
 using tile::block_exscan_mod;
 using tile::block_reduce_mod;
-using tile::sidx;
 using tile::to_unit;
 
 // The default tile (128 threads x 16 outputs on the CRT route) also has an
@@ -52,23 +52,150 @@ constexpr bool tuned_tile()
     return L == 16 && MODEXP == MODEXP_CRT32;
 }
 
-// U < L: the encryption runs in passes of U chains (the unroll knob).
-template <int L, int MODEXP, int DIV, int TB, int U = L>
-__global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
-    k_generate(DeviceTables tab, const WorkItem *__restrict__ items,
-                                                  uint32_t nitems, uint32_t *ticket,
-                                                  double *__restrict__ out_r,
-                                                  u64 *__restrict__ out_c, u64 stride)
+// Staging of a tile for bulk tensor stores (the layout of a 128-byte
+// swizzled tensor map): element i lies in 128-byte line i / 16, and its
+// 16-byte chunk (i / 2) % 8 sits at chunk position ((i / 2) % 8) ^ (line % 8).
+// A thread writes its run as 16-byte chunks; the eight lanes of one
+// shared-memory wavefront then hit eight different chunk positions.
+__device__ __forceinline__ int swz(int i)
 {
+    const int line = i >> 4;
+    return (line << 4) | (((((i >> 1) & 7) ^ (line & 7))) << 1) | (i & 1);
+}
+
+// Elements per staging buffer: a tile, and with two buffers (shifted
+// staging) one more 16-element line, rounded to keep buffers 1 KB aligned.
+__host__ __device__ constexpr int stage_elements(int S, int nbuf)
+{
+    return nbuf == 2 ? S + 128 : S;
+}
+
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One bulk tensor store per box of rows: rows 16-element lines from the
+// swizzled staging src to lines row0 .. row0 + rows - 1 of the view.
+__device__ __forceinline__ void bulk_store_rows(const CUtensorMap *map, const u64 *src, int rows,
+                                                int box_rows, u64 row0)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(src);
+    for (int b = 0; b < rows; b += box_rows)
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     :
+                     : "l"((u64)map), "r"(0), "r"((int)(row0 + (u64)b)), "r"(s + (uint32_t)b * 128u)
+                     : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// A thread's run of L values to the swizzled staging positions p0 .. p0 +
+// L - 1, in 16-byte chunks where the positions allow (p0 even), else as a
+// single first and last element around L / 2 - 1 chunks. p0 = my0 (the
+// unshifted staging) keeps the positions visible to the compiler.
+template <int L>
+__device__ __forceinline__ void stage_run(u64 *st, int my0, int shift, const u64 (&v)[L])
+{
+    if (shift == 0) {
+#pragma unroll
+        for (int k = 0; k < L / 2; k++)
+            *reinterpret_cast<ulonglong2 *>(st + swz(my0 + 2 * k)) =
+                make_ulonglong2(v[2 * k], v[2 * k + 1]);
+        return;
+    }
+    const int p0 = my0 + shift;
+    if ((p0 & 1) == 0) {
+#pragma unroll
+        for (int k = 0; k < L / 2; k++)
+            *reinterpret_cast<ulonglong2 *>(st + swz(p0 + 2 * k)) =
+                make_ulonglong2(v[2 * k], v[2 * k + 1]);
+    } else {
+        st[swz(p0)] = v[0];
+#pragma unroll
+        for (int k = 1; k < L / 2; k++)
+            *reinterpret_cast<ulonglong2 *>(st + swz(p0 + 2 * k - 1)) =
+                make_ulonglong2(v[2 * k - 1], v[2 * k]);
+        st[swz(p0 + L - 1)] = v[L - 1];
+    }
+}
+
+// Element stores of staged outputs i = t, t + T, ... below n from staging
+// position shift + i to dst[i * stride]. For T a multiple of 128 the
+// swizzled position of shift + t + kT is that of shift + t plus kT (the
+// line advances by a multiple of 8), so it is computed once.
+__device__ __forceinline__ void put(double *p, u64 bits) { *p = __longlong_as_double((long long)bits); }
+__device__ __forceinline__ void put(u64 *p, u64 bits) { *p = bits; }
+
+template <class V>
+__device__ __forceinline__ void store_elements(V *dst, const u64 *st, int n, int shift,
+                                               u64 stride)
+{
+    const int T = blockDim.x, t = threadIdx.x;
+    if ((T & 127) == 0) {
+        for (int i = t, j = swz(shift + t); i < n; i += T, j += T)
+            put(dst + (u64)i * stride, st[j]);
+    } else {
+        for (int i = t; i < n; i += T)
+            put(dst + (u64)i * stride, st[swz(shift + i)]);
+    }
+}
+
+// Waits until the bulk stores issued by this thread have read their source
+// (read = true) or have completed.
+template <bool READ>
+__device__ __forceinline__ void bulk_wait_all()
+{
+    if constexpr (READ)
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    else
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// U < L: the encryption runs in passes of U chains (the unroll knob).
+//
+// Output of a tile. Every thread stages its L outputs in the swizzled layout
+// of one of nbuf staging buffers per output kind; full tiles leave by bulk
+// tensor stores of whole 16-element lines issued by thread 0, other tiles by
+// the block's element stores.
+//  - With two buffers (stride 1, the SHIFT variant) the staging is shifted
+//    by x0 = the item's first output mod 16, so that staging line l holds line (o >> 4) + l of
+//    the arrays. The tile's last x0 outputs then fill the first x0 places of
+//    the next line, which the tile copies to the head of the other buffer:
+//    the next tile stores its first line whole, carried head included. An
+//    item's first tile, when x0 != 0, and its ragged last tile use element
+//    stores (with the carried head); a last full tile stores its tail by
+//    elements. An output written twice is written with the same bits.
+//  - Otherwise a tile is stored in bulk when its first output is a multiple
+//    of 16 elements into the arrays (the variant without SHIFT carries none
+//    of the shift's code: measured 5 % faster at e = 3 with two outputs).
+// A buffer is written again only after its bulk stores have read it: with
+// two buffers thread 0 waits for the stores of the tile before (which had a
+// whole tile of computation to finish) ahead of the barrier that follows the
+// staging; with one it waits ahead of an extra barrier before the staging.
+// Thread 0 waits for all its bulk stores to complete before the block exits.
+template <int L, int MODEXP, int DIV, int TB, int U = L, bool SHIFT = false>
+__global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
+    k_generate(DeviceTables tab, const WorkItem *__restrict__ items, uint32_t nitems,
+               uint32_t *ticket, double *__restrict__ out_r, u64 *__restrict__ out_c, u64 stride,
+               const __grid_constant__ StoreMaps maps)
+{
+    static_assert(L % 2 == 0, "a thread stages whole 16-byte chunks");
     pdl_wait();  // the start states of the pieces, from the start-state scan
     extern __shared__ u64 smem[];
     __shared__ u64 sh_scan[32];
     __shared__ uint32_t sh_item;
     const int T = blockDim.x, t = threadIdx.x;
     const int S = T * L;
-    const int slots = S + (S >> 4);
-    u64 *st_r = smem;
-    u64 *st_c = smem + (out_r ? slots : 0);
+    // staging buffers, 1024-byte aligned (the swizzle pattern repeats every 1 KB)
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    u64 *const stage = smem + (((sbase + 1023u) & ~1023u) - sbase) / 8;
+    const int kinds = (out_r ? 1 : 0) + (out_c ? 1 : 0);
+    const int nbuf = maps.nbuf;
+    const bool shifted = SHIFT && nbuf == 2 && stride == 1;
+    const int SB = stage_elements(S, nbuf);  // elements per staging buffer
+    const int rows = S >> 4;
+    uint32_t tiles = 0;    // tiles this block has staged
+    bool pending = false;  // thread 0: bulk stores issued and not yet waited for
 
     uint32_t it = blockIdx.x;
     if (ticket) {
@@ -94,6 +221,7 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
         u64 s_thr = mulmodQ(s, plin[t * L]);
         const u64 aS = plin[S];
         const u64 count = W.count;
+        const int x0 = shifted ? (int)(W.out_off & 15) : 0;
         for (u64 base = 0; base < count; base += S) {
             const u64 left = count - base;
             const int tile_n = left < (u64)S ? (int)left : S;
@@ -102,38 +230,73 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
             u64 c[L], total;
             tile::tile_ciphertexts<L, MODEXP, U>(tab, W, P, m, s_thr, left, my0, nvalid, sh_scan, c,
                                               total);
+            const int b = (int)(tiles % (uint32_t)nbuf);
+            u64 *const st_r = stage + (size_t)b * kinds * SB;
+            u64 *const st_c = st_r + (out_r ? SB : 0);
+            if (nbuf == 1) {
+                if (t == 0 && pending)
+                    bulk_wait_all<true>();
+                __syncthreads();
+            }
+            if (out_r && x0 == 0) {  // each pair divided as it is staged (fewer live registers)
 #pragma unroll
-            for (int j = 0; j < L; j++) {
-                const int i = sidx(my0 + j);
+                for (int k = 0; k < L / 2; k++)
+                    *reinterpret_cast<ulonglong2 *>(st_r + swz(my0 + 2 * k)) = make_ulonglong2(
+                        (u64)__double_as_longlong(to_unit<DIV>(c[2 * k], P, 2 * k)),
+                        (u64)__double_as_longlong(to_unit<DIV>(c[2 * k + 1], P, 2 * k + 1)));
+            } else if (out_r) {
+                u64 v[L];
+#pragma unroll
+                for (int j = 0; j < L; j++)
+                    v[j] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
+                stage_run<L>(st_r, my0, x0, v);
+            }
+            if (out_c)
+                stage_run<L>(st_c, my0, x0, c);
+            const u64 o = W.out_off + base * stride;
+            const bool first = base == 0, last = left <= (u64)S;
+            const bool bulk = maps.extent && stride == 1 && tile_n == S &&
+                              (int)(o & 15) == x0 && (x0 == 0 || !first) &&
+                              o - x0 + (u64)S <= maps.extent;
+            if (bulk)
+                fence_async_shared();  // the staging, visible to the bulk copies
+            if (nbuf == 2 && t == 0 && pending)
+                bulk_wait_all<true>();
+            __syncthreads();
+            tiles++;
+            if (bulk) {
+                if (t == 0) {
+                    if (out_r)
+                        bulk_store_rows(&maps.r, st_r, rows, maps.box_rows, (o - x0) >> 4);
+                    if (out_c)
+                        bulk_store_rows(&maps.c, st_c, rows, maps.box_rows, (o - x0) >> 4);
+                    pending = true;
+                }
+                if (last && t < x0) {  // the tail beyond the last whole line
+                    if (out_r)
+                        put(out_r + o + S - x0 + t, st_r[swz(S + t)]);
+                    if (out_c)
+                        put(out_c + o + S - x0 + t, st_c[swz(S + t)]);
+                }
+            } else {
                 if (out_r)
-                    st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
+                    store_elements(out_r + o, st_r, tile_n, x0, stride);
                 if (out_c)
-                    st_c[i] = c[j];
-            }
-            __syncthreads();
-            if (stride == 1) {
-                const u64 o = W.out_off + base;
-                if (out_r) {
-                    for (int i = t; i < tile_n; i += T)
-                        out_r[o + i] = __longlong_as_double((long long)st_r[sidx(i)]);
-                }
-                if (out_c) {
-                    for (int i = t; i < tile_n; i += T)
-                        out_c[o + i] = st_c[sidx(i)];
-                }
-            } else {  // interleaved order: outputs of the item stride elements apart
-                const u64 o = W.out_off + base * stride;
-                if (out_r) {
-                    for (int i = t; i < tile_n; i += T)
-                        out_r[o + (u64)i * stride] =
-                            __longlong_as_double((long long)st_r[sidx(i)]);
-                }
-                if (out_c) {
-                    for (int i = t; i < tile_n; i += T)
-                        out_c[o + (u64)i * stride] = st_c[sidx(i)];
+                    store_elements(out_c + o, st_c, tile_n, x0, stride);
+                if (!first && t < x0) {  // the carried head, which a bulk tile leaves
+                    if (out_r)
+                        put(out_r + o - x0 + t, st_r[swz(t)]);
+                    if (out_c)
+                        put(out_c + o - x0 + t, st_c[swz(t)]);
                 }
             }
-            __syncthreads();
+            if (!last && t < x0) {  // carry the tail to the head of the other buffer
+                const size_t nb = (size_t)(1 - b) * kinds * SB;
+                if (out_r)
+                    stage[nb + swz(t)] = st_r[swz(S + t)];
+                if (out_c)
+                    stage[nb + (out_r ? SB : 0) + swz(t)] = st_c[swz(S + t)];
+            }
             m = addmod(m, total, n);
             s_thr = mulmodQ(s_thr, aS);
         }
@@ -152,6 +315,8 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
             it += gridDim.x;
         }
     }
+    if (t == 0 && pending)
+        bulk_wait_all<false>();
 }
 
 // Skip sums of chunks: for chunk k with start offset o and length len,
@@ -273,13 +438,98 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
     }
 }
 
+// shift: a launch whose stores may go in bulk with two staging buffers
+// (shifted staging); the default tile has that variant.
 template <int L, int MODEXP, int DIV, int U = L>
-auto gen_kernel(int threads)
+auto gen_kernel(int threads, bool shift = false)
 {
-    if constexpr (tuned_tile<L, MODEXP>())
+    if constexpr (tuned_tile<L, MODEXP>()) {
+        if constexpr (U == L)
+            if (threads == kTunedThreads && shift)
+                return k_generate<L, MODEXP, DIV, kTunedThreads, U, true>;
         if (threads == kTunedThreads)
             return k_generate<L, MODEXP, DIV, kTunedThreads, U>;
+    }
     return k_generate<L, MODEXP, DIV, 0, U>;
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (the library links no driver-API import library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+// The 2-D view [rows][16] of a 64-bit output array, 128-byte swizzled, boxes
+// of box_rows lines.
+bool encode_view(CUtensorMap *m, void *base, uint64_t rows, int box_rows)
+{
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc)
+        return false;
+    const cuuint64_t dims[2] = {16, rows};
+    const cuuint64_t strides[1] = {16 * sizeof(uint64_t)};
+    const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Whether p is (null or) device memory: page-locked host memory that the
+// kernel writes through its mapping keeps the element stores.
+bool device_or_null(const void *p)
+{
+    if (!p)
+        return true;
+    // The query enqueues nothing; relaxed capture mode for this thread keeps it
+    // legal while a caller captures the stream into a graph.
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    cudaPointerAttributes at{};
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice;
+}
+
+// The store maps of a launch: bulk stores need the contiguous order, a known
+// output extent of at least one tile (and fewer than 2^31 lines, the range of
+// a tensor coordinate), and 16-byte aligned arrays in device memory.
+StoreMaps store_maps(const GenLaunch &g, int L, double *out_r, uint64_t *out_c)
+{
+    StoreMaps maps;
+    memset(&maps, 0, sizeof maps);
+    maps.nbuf = gen_stage_buffers(g.threads, L, out_r != nullptr, out_c != nullptr);
+    const int lines = g.threads * L / 16;
+    maps.box_rows = lines < 256 ? lines : 256;
+    const uint64_t rows = g.out_extent / 16;
+    const bool aligned = ((uintptr_t)out_r % 16) == 0 && ((uintptr_t)out_c % 16) == 0;
+    if (g.stride != 1 || rows < (uint64_t)lines || rows >= (1ULL << 31) || !aligned ||
+        !device_or_null(out_r) || !device_or_null(out_c))
+        return maps;
+    if (out_r && !encode_view(&maps.r, out_r, rows, maps.box_rows))
+        return maps;
+    if (out_c && !encode_view(&maps.c, out_c, rows, maps.box_rows))
+        return maps;
+    maps.extent = rows * 16;
+    return maps;
 }
 
 template <int L, int MODEXP, int DIV, int U = L>
@@ -288,7 +538,8 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
                          cudaStream_t stream)
 {
     const size_t smem = gen_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
-    auto kern = gen_kernel<L, MODEXP, DIV, U>(g.threads);
+    const StoreMaps maps = store_maps(g, L, out_r, out_c);
+    auto kern = gen_kernel<L, MODEXP, DIV, U>(g.threads, maps.extent && maps.nbuf == 2);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -296,7 +547,7 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
             return e;
     }
     return launch_kernel(kern, g.grid, g.threads, smem, stream, g.pdl, t, items, nitems,
-                         g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride);
+                         g.persistent ? ticket : nullptr, out_r, out_c, (u64)g.stride, maps);
 }
 
 template <int L, int MODEXP, int DIV, int U = L>
@@ -523,7 +774,24 @@ cudaError_t time_it(F &&launch, cudaStream_t stream, float *ms)
 
 }  // namespace
 
+// Two staging buffers per output kind (one barrier per tile fewer) while
+// they take at most 40 KB, which keeps five 128-thread blocks of 16 outputs
+// per thread on an SM; else one.
+int gen_stage_buffers(int threads, int L, bool want_r, bool want_c)
+{
+    const size_t bytes = (size_t)threads * L * 8 * ((want_r ? 1 : 0) + (want_c ? 1 : 0));
+    return 2 * bytes <= 40 * 1024 ? 2 : 1;
+}
+
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c)
+{
+    const int nbuf = gen_stage_buffers(threads, L, want_r, want_c);
+    return (size_t)nbuf * stage_elements(threads * L, nbuf) * 8 *
+               ((want_r ? 1 : 0) + (want_c ? 1 : 0)) +
+           1024;
+}
+
+size_t padded_smem_bytes(int threads, int L, bool want_r, bool want_c)
 {
     const size_t S = (size_t)threads * L;
     const size_t slots = S + (S >> 4);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda.h>  // CUtensorMap (the type only; no driver-API link)
 #include <cuda_runtime.h>
 
 #include "host_params.hpp"
@@ -45,6 +46,20 @@ struct GenLaunch {
     int unroll = 0;    // 0 or >= L: all L chains at once; else passes of this many
     int L_wide = 0;    // vector kernel: the configured numbers per thread, which
                        // whole-warp segments may run instead of L
+    uint64_t out_extent = 0;  // stride 1: elements of the output arrays the launch may
+                              // write (0: unknown, no bulk tensor stores)
+};
+
+// Bulk tensor stores of the generation kernel's tiles. The output arrays are
+// viewed as 2-D tensors [extent / 16][16] of 64-bit elements with 128-byte
+// swizzling; a block stages a whole tile in that swizzled layout and one
+// thread writes it with cp.async.bulk.tensor, one copy per box of rows.
+struct alignas(128) StoreMaps {
+    CUtensorMap r;    // view of out_r
+    CUtensorMap c;    // view of out_c
+    uint64_t extent;  // elements both views cover (a multiple of 16); 0: no bulk stores
+    int box_rows;     // 16-element rows per bulk copy (at most 256)
+    int nbuf;         // staging buffers per output kind (1 or 2)
 };
 
 // Launches kern; with pdl as a programmatic dependent of the kernel before it
@@ -67,8 +82,13 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// Shared memory bytes the generation kernel needs for a tile.
+// Shared memory bytes the generation kernel needs for a tile: its staging
+// buffers (gen_stage_buffers per output kind) and 1 KB to align them.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
+int gen_stage_buffers(int threads, int L, bool want_r, bool want_c);
+// The padded staging of the vector and single-launch kernels: one 8-byte pad
+// slot every 16 elements, per output kind.
+size_t padded_smem_bytes(int threads, int L, bool want_r, bool want_c);
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c);
 // Numbers per thread the vector kernel uses for a configured L: the tuned

@@ -262,7 +262,7 @@ template <int L, int MODEXP, int DIV>
 cudaError_t launch_lb_t(int threads, const DeviceTables &tab, const LbArgs &A, double *out_r,
                         u64 *out_c, cudaStream_t stream)
 {
-    const size_t smem = gen_smem_bytes(threads, L, out_r != nullptr, out_c != nullptr);
+    const size_t smem = padded_smem_bytes(threads, L, out_r != nullptr, out_c != nullptr);
     auto kern = k_generate_lookback<L, MODEXP, DIV>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -306,7 +306,7 @@ int latency_occupancy(bool exact, bool both)
     if (o < 0) {
         const void *k = exact ? (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_EXACT>
                               : (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_INT>;
-        const size_t smem = gen_smem_bytes(512, 16, true, both);
+        const size_t smem = padded_smem_bytes(512, 16, true, both);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int b = 0;

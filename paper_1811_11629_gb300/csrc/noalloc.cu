@@ -143,6 +143,7 @@ int rsaprng_generate_f64_noalloc(rsaprng_ctx *c, rsaprng_id id, uint64_t N, doub
     }
     GenLaunch g = ctx_launch(c, c->cfg, nchunks, true, false);
     g.pdl = nchunks > 1;  // right after the start-state scan
+    g.out_extent = N;
     if ((e = launch_generate(g, t, S->items, nchunks, &S->ticket, d_r, nullptr, st)) !=
         cudaSuccess)
         return RSAPRNG_ERR_CUDA;

@@ -121,6 +121,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     hp.chunks.clear();
     hp.groups.clear();
     hp.numbers = 0;
+    hp.extent = 0;
     hp.stride = stride;
     hp.vecs.clear();
     hp.vec_ts = 0;
@@ -221,6 +222,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
                 const uint64_t room = cut - (off % cut);
                 const uint64_t len = std::min(left, room);
                 pieces.push_back({off, len, out});
+                hp.extent = std::max(hp.extent, out + (len - 1) * stride + 1);
                 off += len;
                 out += len * stride;
                 left -= len;

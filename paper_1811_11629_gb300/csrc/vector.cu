@@ -333,7 +333,7 @@ int vec_numbers_per_thread(int L, int modexp, int threads)
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c)
 {
-    return gen_smem_bytes(threads, L, want_r, want_c);  // the same padded slots
+    return padded_smem_bytes(threads, L, want_r, want_c);  // the same padded slots
 }
 
 cudaError_t launch_generate_vec(const GenLaunch &g0, const DeviceTables &t, const WorkItem *items,

@@ -120,15 +120,20 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
 
     // 1. coverage and stream order: stream position -> element, per instance
     std::map<uint32_t, std::vector<uint64_t>> want;  // instance -> element of each position
-    uint64_t total = 0;
+    uint64_t total = 0, extent = 0;
     for (size_t i = 0; i < ids.size(); i++) {
         auto &v = want[ids[i]];
         for (uint64_t k = 0; k < counts[i]; k++)
             v.push_back(offsets[i] + k * stride);
         total += counts[i];
+        if (counts[i])
+            extent = std::max(extent, offsets[i] + (counts[i] - 1) * stride + 1);
     }
     CHECK(hp.numbers == total, "numbers %llu != %llu", (unsigned long long)hp.numbers,
           (unsigned long long)total);
+    // the extent bounds the bulk stores' view of the output arrays
+    CHECK(hp.extent == extent, "extent %llu != %llu", (unsigned long long)hp.extent,
+          (unsigned long long)extent);
     std::map<uint32_t, std::vector<uint64_t>> got;  // instance -> (position -> element)
     std::map<uint32_t, std::vector<size_t>> items_of;
     uint64_t sum_items = 0;

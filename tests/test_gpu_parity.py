@@ -112,6 +112,52 @@ def test_routes_and_tilings_ragged(O, modexp, divide, threads, L):
             off += n
 
 
+@pytest.mark.parametrize("both", [False, True])
+@pytest.mark.parametrize("threads,L", [(128, 16), (512, 16), (64, 2), (256, 8), (128, 4)])
+def test_bulk_tensor_stores(O, threads, L, both):
+    """Full tiles leave by bulk tensor stores of whole 16-element lines (2-D swizzled views
+    of the output arrays; two boxes per tile at 512 x 16). Streams that start at an offset
+    of 16k + x0 are staged shifted by x0 (one output kind: two staging buffers), each
+    tile's last x0 outputs carried into the next tile's first line; other tiles use
+    element stores: a piece's first tile when x0 != 0, ragged ends, full last tiles' tails,
+    and everything when the arrays are 8 bytes off 16-byte alignment (second call). Two
+    output kinds (one buffer): bulk only at multiples of 16. Offsets 16k, 16k + 6, 16k + 5,
+    16k + 11; pieces of several tiles (one block per SM). Bit-exact with the oracle, and
+    the gaps between the ranges keep their fill."""
+    ctx = R.Context(8, threads_per_block=threads, numbers_per_thread=L, chunk=1 << 20,
+                    blocks_per_sm=1)
+    ids, par = seeded(ctx, O, master=19, k=4, rule=R.E_UNIFORM, lo=3, hi=257)
+    tile = threads * L
+    k = max(3, 400000 // tile)
+    counts = np.array([k * tile, k * tile + 17, k * tile, k * tile + 3], np.uint64)
+    offs, at = [], 0
+    for cnt, x0 in zip(counts, (0, 6, 5, 11)):
+        at = (at + 15) // 16 * 16 + 16 + x0
+        offs.append(at)
+        at += int(cnt)
+    total = at + 16
+    offsets = np.array(offs, np.uint64)
+    states = [(pr[3], 1) for pr in par]
+    for call, shift in enumerate((0, 1)):
+        cbuf = torch.full((total + shift,), 7, dtype=torch.int64, device="cuda")
+        rbuf = torch.full((total + shift,), -1.0, dtype=torch.float64, device="cuda")
+        out_c = cbuf[shift:] if both else None
+        out_r = rbuf[shift:]
+        ctx.generate_batch(ids, counts, out_r=out_r, out_c=out_c, offsets=offsets)
+        torch.cuda.synchronize()
+        gr = rbuf.cpu().numpy()[shift:]
+        gc = cbuf.cpu().numpy().view(np.uint64)[shift:]
+        written = np.zeros(total, bool)
+        for i in range(len(ids)):
+            o, n = offs[i], int(counts[i])
+            written[o:o + n] = True
+            states[i] = check_stream(O, par[i], *states[i], gc[o:o + n] if both else None,
+                                     gr[o:o + n])
+            assert ctx.get_state(int(ids[i])) == states[i]
+        assert (gr[~written] == -1.0).all()
+        assert (gc[~written] == 7).all()
+
+
 @pytest.mark.parametrize("cfg", [
     dict(streams_per_block=2), dict(streams_per_block=4),
     dict(streams_per_block=2, threads_per_block=256), dict(streams_per_block=8, threads_per_block=256),
