@@ -345,6 +345,16 @@ int rsaprng_chi2_uniform(const uint64_t *h_hist, uint64_t bins, double *chi2, ui
 int rsaprng_plan_create(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
                         const uint64_t *counts, const uint64_t *out_offsets, rsaprng_plan **out);
 int rsaprng_plan_launch(rsaprng_plan *plan, double *d_r, uint64_t *d_c, void *stream);
+/* rsaprng_plan_launch that also records the caller's CUDA events gen_start
+ * and gen_end (cudaEvent_t, created by the caller, with timing) on the stream
+ * right before and after the generation kernel, so that their elapsed time is
+ * that kernel's alone; the skip-sum pre-pass and start-state scan, when the
+ * plan has them, run before gen_start, and the generation kernel then starts
+ * after the scan has completed instead of overlapping its end. Same outputs
+ * and state advance as rsaprng_plan_launch. RSAPRNG_ERR_ARG for a null plan,
+ * no output or a null event; RSAPRNG_ERR_CUDA when recording an event fails. */
+int rsaprng_plan_launch_timed(rsaprng_plan *plan, double *d_r, uint64_t *d_c, void *stream,
+                              void *gen_start, void *gen_end);
 int rsaprng_plan_capture(rsaprng_plan *plan, double *d_r, uint64_t *d_c, void *stream);
 int rsaprng_plan_replay(rsaprng_plan *plan, void *stream);
 /* Kernel launches one rsaprng_plan_launch makes, and numbers it generates. */

@@ -328,9 +328,20 @@ class Plan:
                                          _u64p(offsets), ctypes.byref(h)), "plan_create")
         self.h = h
 
-    def launch(self, out_r=None, out_c=None, stream=None):
-        check(self.L.rsaprng_plan_launch(self.h, _dptr(out_r), _dptr(out_c), _stream_ptr(stream)),
-              "plan_launch")
+    def launch(self, out_r=None, out_c=None, stream=None, gen_events=None):
+        """gen_events: a pair of torch.cuda.Event(enable_timing=True) recorded right before
+        and after the generation kernel (its time alone, after the pre-pass)."""
+        if gen_events is None:
+            check(self.L.rsaprng_plan_launch(self.h, _dptr(out_r), _dptr(out_c),
+                                             _stream_ptr(stream)), "plan_launch")
+            return
+        a, b = gen_events
+        for ev in (a, b):
+            if not ev.cuda_event:  # torch creates the CUDA event at its first record
+                ev.record()
+        check(self.L.rsaprng_plan_launch_timed(self.h, _dptr(out_r), _dptr(out_c),
+                                               _stream_ptr(stream), ctypes.c_void_p(a.cuda_event),
+                                               ctypes.c_void_p(b.cuda_event)), "plan_launch_timed")
 
     def capture(self, out_r=None, out_c=None, stream=None):
         check(self.L.rsaprng_plan_capture(self.h, _dptr(out_r), _dptr(out_c), _stream_ptr(stream)),

@@ -84,6 +84,7 @@ SIGNATURES = {
     "rsaprng_chi2_uniform": (i32, [pu64, u64, pdbl, pu64]),
     "rsaprng_plan_create": (i32, [vp, u64, pu32, pu64, pu64, pvp]),
     "rsaprng_plan_launch": (i32, [vp, vp, vp, vp]),
+    "rsaprng_plan_launch_timed": (i32, [vp, vp, vp, vp, vp, vp]),
     "rsaprng_plan_capture": (i32, [vp, vp, vp, vp]),
     "rsaprng_plan_replay": (i32, [vp, vp]),
     "rsaprng_plan_info": (i32, [vp, pu64, pu64, pu64]),

@@ -262,6 +262,7 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
     dp.ngroups = (uint32_t)hp.groups.size();
     dp.numbers = hp.numbers;
     dp.extent = hp.extent;
+    dp.unaligned = hp.unaligned;
     dp.stride = hp.stride;
     dp.nvecs = (uint32_t)hp.vecs.size();
     dp.vec_ts = hp.vec_ts;
@@ -308,7 +309,7 @@ static GenLaunch hist_launch(rsaprng_ctx *c, const rsaprng_config &cfg, uint64_t
 
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
                 uint64_t *d_c, cudaStream_t stream, uint64_t *launches, const HistArgs *hist,
-                bool fresh)
+                bool fresh, const cudaEvent_t *gen_events)
 {
     const DeviceTables t = ctx_tables(c);
     uint64_t nl = 0;
@@ -321,6 +322,7 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
                   : ctx_launch(c, cfg, dp.nitems, d_r != nullptr, d_c != nullptr, &dp.occupancy);
         g.stride = dp.stride;
         g.out_extent = dp.extent;
+        g.out_unaligned = dp.unaligned;
         g.pdl = dp.nchunks > 0;
         dp.last = g;
         // A persistent launch's ticket is reset before the pre-pass, so that the
@@ -341,6 +343,10 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
         nl += 2;
     }
     if (dp.nitems) {
+        // An event between the scan and the generation kernel makes the
+        // latter an ordinary launch (its griddepcontrol.wait returns at once).
+        if (gen_events && (e = cudaEventRecord(gen_events[0], stream)) != cudaSuccess)
+            return cuda_fail(e, "timing event");
         if (hist)
             e = launch_histogram(g, t, dp.items, dp.nitems, dp.ticket, *hist, stream);
         else if (vec)
@@ -350,6 +356,8 @@ int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *
             e = launch_generate(g, t, dp.items, dp.nitems, dp.ticket, d_r, d_c, stream);
         if (e != cudaSuccess)
             return cuda_fail(e, hist ? "histogram launch" : "generate launch");
+        if (gen_events && (e = cudaEventRecord(gen_events[1], stream)) != cudaSuccess)
+            return cuda_fail(e, "timing event");
         nl += 1;
     }
     c->launches += nl;

@@ -31,6 +31,7 @@ struct DevPlan {
     uint32_t nitems = 0, nchunks = 0, ngroups = 0;
     uint64_t numbers = 0;
     uint64_t extent = 0;  // one past the last output element the plan writes
+    bool unaligned = false;  // a piece starts off a multiple of 16 elements
     uint64_t stride = 1;
     VecGroup *vecs = nullptr;
     uint32_t nvecs = 0;
@@ -96,10 +97,12 @@ int upload_plan(rsaprng_ctx *c, const HostPlan &hp, DevPlan &dp, cudaStream_t st
 // consumer instead of the generation kernel when hist is given. fresh: the
 // plan was uploaded for this launch alone, so its work-queue counter is still
 // the zero the upload wrote (a plan launched again, or captured in a graph,
-// resets it on the stream).
+// resets it on the stream). gen_events: two CUDA events recorded on the
+// stream right before and after the generation kernel's launch (or null).
 int launch_plan(rsaprng_ctx *c, const rsaprng_config &cfg, DevPlan &dp, double *d_r,
                 uint64_t *d_c, cudaStream_t stream, uint64_t *launches,
-                const HistArgs *hist = nullptr, bool fresh = false);
+                const HistArgs *hist = nullptr, bool fresh = false,
+                const cudaEvent_t *gen_events = nullptr);
 void free_devplan(DevPlan &dp);
 int scratch_slot(rsaprng_ctx *c, ScratchSlot **out);
 // One instance's N outputs in one launch with a decoupled look-back, when the

@@ -438,8 +438,9 @@ __global__ void __launch_bounds__(kScanT) k_prep_scan(DeviceTables tab,
     }
 }
 
-// shift: a launch whose stores may go in bulk with two staging buffers
-// (shifted staging); the default tile has that variant.
+// shift: a launch whose stores may go in bulk with two staging buffers and
+// whose items do not all start at multiples of 16 elements (shifted
+// staging); the default tile has that variant.
 template <int L, int MODEXP, int DIV, int U = L>
 auto gen_kernel(int threads, bool shift = false)
 {
@@ -539,7 +540,8 @@ cudaError_t launch_gen_t(const GenLaunch &g, const DeviceTables &t, const WorkIt
 {
     const size_t smem = gen_smem_bytes(g.threads, L, out_r != nullptr, out_c != nullptr);
     const StoreMaps maps = store_maps(g, L, out_r, out_c);
-    auto kern = gen_kernel<L, MODEXP, DIV, U>(g.threads, maps.extent && maps.nbuf == 2);
+    auto kern = gen_kernel<L, MODEXP, DIV, U>(g.threads,
+                                              maps.extent && maps.nbuf == 2 && g.out_unaligned);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -48,6 +48,7 @@ struct GenLaunch {
                        // whole-warp segments may run instead of L
     uint64_t out_extent = 0;  // stride 1: elements of the output arrays the launch may
                               // write (0: unknown, no bulk tensor stores)
+    bool out_unaligned = false;  // some item starts off a multiple of 16 elements
 };
 
 // Bulk tensor stores of the generation kernel's tiles. The output arrays are

@@ -122,6 +122,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
     hp.groups.clear();
     hp.numbers = 0;
     hp.extent = 0;
+    hp.unaligned = false;
     hp.stride = stride;
     hp.vecs.clear();
     hp.vec_ts = 0;
@@ -223,6 +224,7 @@ int build_plan_core(const InstParams *params, uint64_t ninst, int modexp, const 
                 const uint64_t len = std::min(left, room);
                 pieces.push_back({off, len, out});
                 hp.extent = std::max(hp.extent, out + (len - 1) * stride + 1);
+                hp.unaligned |= stride == 1 && (out & 15) != 0;
                 off += len;
                 out += len * stride;
                 left -= len;

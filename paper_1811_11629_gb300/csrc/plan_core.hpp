@@ -17,6 +17,7 @@ struct HostPlan {
     uint64_t numbers = 0;
     uint64_t stride = 1;  // element distance between consecutive outputs of a request
     uint64_t extent = 0;  // one past the last output element the plan writes
+    bool unaligned = false;  // stride 1: a piece starts off a multiple of 16 elements
     std::vector<VecGroup> vecs;  // stride > 1: blocks' units of the vector kernel
     int vec_ts = 0;              // threads per instance in the vector kernel
     // Working storage of the planner, kept so that a plan rebuilt in the same

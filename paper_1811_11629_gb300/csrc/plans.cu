@@ -120,6 +120,17 @@ int rsaprng_plan_launch(rsaprng_plan *p, double *d_r, uint64_t *d_c, void *strea
     return launch_plan(p->ctx, p->cfg, p->dp, d_r, d_c, (cudaStream_t)stream, nullptr);
 }
 
+int rsaprng_plan_launch_timed(rsaprng_plan *p, double *d_r, uint64_t *d_c, void *stream,
+                              void *gen_start, void *gen_end)
+{
+    if (!p || (!d_r && !d_c) || !gen_start || !gen_end)
+        return fail(RSAPRNG_ERR_ARG, "plan_launch_timed: bad arguments");
+    cudaSetDevice(p->ctx->device);
+    const cudaEvent_t ev[2] = {(cudaEvent_t)gen_start, (cudaEvent_t)gen_end};
+    return launch_plan(p->ctx, p->cfg, p->dp, d_r, d_c, (cudaStream_t)stream, nullptr, nullptr,
+                       false, ev);
+}
+
 int rsaprng_plan_capture(rsaprng_plan *p, double *d_r, uint64_t *d_c, void *stream)
 {
     if (!p || (!d_r && !d_c) || !stream)

@@ -37,6 +37,11 @@ double now_s()
 }
 
 // First-fit allocator over [0, capacity) elements with coalescing frees.
+// Allocations are whole 16-element (128-byte) lines, so every result starts
+// on a line and the iterations' full tiles leave by bulk tensor stores
+// without a staging shift.
+static uint64_t whole_lines(uint64_t n) { return (n + 15) & ~15ULL; }
+
 class Arena {
   public:
     explicit Arena(uint64_t cap) : cap_(cap) { free_[0] = cap; }
@@ -46,6 +51,7 @@ class Arena {
             *off = 0;
             return true;
         }
+        n = whole_lines(n);
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second >= n) {
                 *off = it->first;
@@ -63,6 +69,7 @@ class Arena {
     {
         if (n == 0)
             return;
+        n = whole_lines(n);
         used_ -= n;
         auto it = free_.emplace(off, n).first;
         auto nx = std::next(it);
@@ -385,13 +392,15 @@ int rsaprng_server_create(rsaprng_ctx *c, uint64_t out_budget_bytes, int nstream
     S->ctx = c;
     S->budget_numbers = out_budget_bytes / 8;
     cudaSetDevice(c->device);
-    cudaError_t e = cudaMalloc(&S->d_arena, S->budget_numbers * 8);
+    // whole lines: a request of the whole budget still fits after rounding
+    const uint64_t cap = whole_lines(S->budget_numbers);
+    cudaError_t e = cudaMalloc(&S->d_arena, cap * 8);
     if (e != cudaSuccess) {
         delete S;
         return fail(RSAPRNG_ERR_OOM, "server arena (%llu B): %s",
                     (unsigned long long)out_budget_bytes, cudaGetErrorString(e));
     }
-    S->arena = new Arena(S->budget_numbers);
+    S->arena = new Arena(cap);
     S->slots.resize(nstreams);
     for (auto &sl : S->slots) {
         cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);

@@ -134,6 +134,11 @@ static void check_case(std::mt19937_64 &rng, bool vector_order)
     // the extent bounds the bulk stores' view of the output arrays
     CHECK(hp.extent == extent, "extent %llu != %llu", (unsigned long long)hp.extent,
           (unsigned long long)extent);
+    // the shifted staging is chosen when some piece starts off a 16-element line
+    bool unaligned = false;
+    for (const WorkItem &w : hp.items)
+        unaligned |= stride == 1 && (w.out_off & 15) != 0;
+    CHECK(hp.unaligned == unaligned, "unaligned flag %d != %d", (int)hp.unaligned, (int)unaligned);
     std::map<uint32_t, std::vector<uint64_t>> got;  // instance -> (position -> element)
     std::map<uint32_t, std::vector<size_t>> items_of;
     uint64_t sum_items = 0;

@@ -466,6 +466,42 @@ def test_plan_graph_replay_persistent_chunked(O):
     plan.close()
 
 
+def test_plan_launch_timed(O):
+    """The timed plan launch (events around the generation kernel alone) continues every
+    stream exactly as the plain launch does, with the pre-pass and scan before the first
+    event; its events bracket a positive time no longer than the whole launch's; a null
+    event is an argument error that launches nothing."""
+    ctx = R.Context(64, chunk=4096)
+    ids, par = seeded(ctx, O, master=24, k=12, rule=R.E_UNIFORM, lo=3, hi=257)
+    counts = np.full(len(ids), 50000, np.uint64)
+    total = int(counts.sum())
+    plan = ctx.plan(ids, counts)
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    states = [(pr[3], 1) for pr in par]
+    for rep in range(3):
+        whole = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        gen = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        whole[0].record()
+        if rep == 1:
+            plan.launch(out_r=out)
+        else:
+            plan.launch(out_r=out, gen_events=gen)
+        whole[1].record()
+        torch.cuda.synchronize()
+        if rep != 1:
+            assert 0 < gen[0].elapsed_time(gen[1]) <= whole[0].elapsed_time(whole[1])
+        g = out.cpu().numpy()
+        for i in range(len(ids)):
+            n = int(counts[i])
+            states[i] = check_stream(O, par[i], *states[i], None, g[i * n:(i + 1) * n])
+    rc = ctx.L.rsaprng_plan_launch_timed(plan.h, out.data_ptr(), None,
+                                         torch.cuda.current_stream().cuda_stream, None, None)
+    assert rc == R._lib.CODES["ERR_ARG"]
+    assert [ctx.get_state(int(i)) for i in ids] == [s_ for s_ in states]
+    assert plan.info()["chunks"] > 100
+    plan.close()
+
+
 def test_autotune_bit_identical_and_state_preserved(O):
     ctx = R.Context(64)
     ids, par = seeded(ctx, O, master=21, k=24, rule=R.E_UNIFORM, lo=3, hi=65537)

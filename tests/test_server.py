@@ -43,6 +43,8 @@ def test_server_mix_equals_alone(O):
     got = []
     for t in tickets:
         srv.wait(t, timeout_s=120)
+        ptr, n = srv.result_ptr(t)
+        assert ptr % 128 == 0  # results start on whole 16-element lines of the arena
         got.append(srv.result(t).cpu().numpy())
         srv.release(t)
     # oracle: each instance alone, requests concatenated in submission order
