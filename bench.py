@@ -617,10 +617,14 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     tuned = ctx.config()
     srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
     mean_cnt = float(cnt.mean())
-    # capacity: all requests at once (arrival 0), the server batching freely
-    srv.replay(pick, cnt, np.zeros(nreq), timeout_s=300)
-    st0 = srv.stats()
-    cap_numbers = st0["numbers_done"] / max(st0["wall_s"], 1e-9)
+    # capacity: all requests at once (arrival 0), the server batching freely; the median
+    # of three replays (one takes about 45 ms)
+    caps = []
+    for _ in range(3):
+        srv.replay(pick, cnt, np.zeros(nreq), timeout_s=300)
+        st0 = srv.stats()
+        caps.append(st0["numbers_done"] / max(st0["wall_s"], 1e-9))
+    cap_numbers = sorted(caps)[1]
     cap_rate = cap_numbers / mean_cnt
     points = []
     for f in loads:
@@ -648,6 +652,7 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     mid = points[len(points) // 2]
     return {"value": round(cap_numbers / 1e9, 3), "unit": UNIT,
             "capacity_req_per_s": round(cap_rate, 1), "requests_per_point": nreq,
+            "capacity_of_replays": [round(x / 1e9, 3) for x in caps],
             "mean_count": round(mean_cnt, 1), "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
             "at_load": mid["load"],
             "config": {x: tuned[x] for x in TUNED_KEYS if x in tuned},
