@@ -271,7 +271,10 @@ int rsaprng_generate_f64_noalloc(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, do
  * instance ids[i] into d_r/d_c at element offset out_offsets[i] (either
  * output may be NULL). ids, counts, out_offsets are HOST arrays. Requests of
  * the same instance are served in array order (each continues after the
- * previous one). */
+ * previous one). Device arrays that start on a 16-byte boundary are written
+ * by bulk tensor stores of whole tiles (faster; the bits are the same);
+ * other arrays, and page-locked host memory mapped into the device, by
+ * element stores. */
 int rsaprng_generate_batch(rsaprng_ctx *ctx, uint64_t nreq, const rsaprng_id *ids,
                            const uint64_t *counts, const uint64_t *out_offsets, double *d_r,
                            uint64_t *d_c, void *stream);

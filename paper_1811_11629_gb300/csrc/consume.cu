@@ -27,7 +27,9 @@ using tile::to_unit;
 
 // floor(r d), exactly, for a double r in [0, 1) and d < 2^32. A normal r is
 // M 2^(E - 1075) with M its 53-bit significand and E its biased exponent, so
-// floor(r d) = (M d) >> (1075 - E) with M d < 2^85; subnormal r give 0.
+// floor(r d) = (M d) >> (1075 - E) with M d < 2^85; subnormal r give 0. For
+// d = 2^k it is M >> (1075 - E - k), a shift (the shift is at least 22, so
+// the result fits 32 bits), which spares the multiply pipe the product.
 __device__ __forceinline__ uint32_t digit_of_unit(double r, uint32_t d)
 {
     const u64 b = (u64)__double_as_longlong(r);
@@ -36,6 +38,10 @@ __device__ __forceinline__ uint32_t digit_of_unit(double r, uint32_t d)
         return 0;
     const u64 M = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
     const int sh = 1075 - E;  // >= 53 since r < 1
+    if ((d & (d - 1)) == 0) {
+        const int s2 = sh - (__ffs(d) - 1);
+        return s2 >= 64 ? 0u : (uint32_t)(M >> s2);
+    }
     const u64 lo = M * d, hi = __umul64hi(M, (u64)d);
     if (sh >= 128)
         return 0;

@@ -288,6 +288,7 @@ cudaError_t launch_lookback(int L, int modexp, int divide, int threads, const De
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_EXACT)
     RSAPRNG_LB(8, MODEXP_CRT32, DIVIDE_RECIP)
+    RSAPRNG_LB(8, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_LB(8, MODEXP_MONT64, DIVIDE_RECIP)
     RSAPRNG_LB(8, MODEXP_MONT64, DIVIDE_INT)
 #undef RSAPRNG_LB
