@@ -57,6 +57,7 @@ def _draw(ctx, i, n, both=True):
     dict(rounding=2),                                          # exact-rational reading
     dict(threads_per_block=64), dict(threads_per_block=512),
     dict(numbers_per_thread=8),
+    dict(numbers_per_thread=8, divide=R.DIVIDE_INT, threads_per_block=512),
     dict(modexp=R.MODEXP_MONT64, numbers_per_thread=8),
     dict(modexp=R.MODEXP_MONT64, numbers_per_thread=8, divide=R.DIVIDE_INT),
 ])
