@@ -615,7 +615,9 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     # iterations do (its 256 x 16 choice served 94.7 Gnumbers/s against 104.5 for the
     # default), so the served form runs what a server gets without tuning.
     tuned = ctx.config()
-    srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=3)
+    # four streams: measured 105.1 capacity and p99 0.69 ms at half load, against 103.6 and
+    # 0.70 with three, 97.5 with two, 104.9 with six and 100.7 with eight
+    srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=4)
     mean_cnt = float(cnt.mean())
     # capacity: all requests at once (arrival 0), the server batching freely; the median
     # of three replays (one takes about 45 ms)

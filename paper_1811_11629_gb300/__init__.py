@@ -376,7 +376,7 @@ class Plan:
 class Server:
     """Continuous-batching server (rsaprng_server)."""
 
-    def __init__(self, ctx: Context, out_budget_bytes: int, nstreams: int = 2):
+    def __init__(self, ctx: Context, out_budget_bytes: int, nstreams: int = 4):
         self.ctx = ctx
         self.L = ctx.L
         h = ctypes.c_void_p()
