@@ -34,8 +34,16 @@ using dev::reduce_u64;
 
 namespace {
 
+using tile::bulk_store_rows;
+using tile::bulk_wait_all;
+using tile::fence_async_shared;
 using tile::FULL;
 using tile::pdl_trigger;
+using tile::put;
+using tile::stage_elements;
+using tile::stage_run;
+using tile::store_elements;
+using tile::swz;
 using tile::pdl_wait;
 using tile::block_exscan_mod;
 using tile::block_reduce_mod;
@@ -50,105 +58,6 @@ template <int L, int MODEXP>
 constexpr bool tuned_tile()
 {
     return L == 16 && MODEXP == MODEXP_CRT32;
-}
-
-// Staging of a tile for bulk tensor stores (the layout of a 128-byte
-// swizzled tensor map): element i lies in 128-byte line i / 16, and its
-// 16-byte chunk (i / 2) % 8 sits at chunk position ((i / 2) % 8) ^ (line % 8).
-// A thread writes its run as 16-byte chunks; the eight lanes of one
-// shared-memory wavefront then hit eight different chunk positions.
-__device__ __forceinline__ int swz(int i)
-{
-    const int line = i >> 4;
-    return (line << 4) | (((((i >> 1) & 7) ^ (line & 7))) << 1) | (i & 1);
-}
-
-// Elements per staging buffer: a tile, and with two buffers (shifted
-// staging) one more 16-element line, rounded to keep buffers 1 KB aligned.
-__host__ __device__ constexpr int stage_elements(int S, int nbuf)
-{
-    return nbuf == 2 ? S + 128 : S;
-}
-
-__device__ __forceinline__ void fence_async_shared()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One bulk tensor store per box of rows: rows 16-element lines from the
-// swizzled staging src to lines row0 .. row0 + rows - 1 of the view.
-__device__ __forceinline__ void bulk_store_rows(const CUtensorMap *map, const u64 *src, int rows,
-                                                int box_rows, u64 row0)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(src);
-    for (int b = 0; b < rows; b += box_rows)
-        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                     :
-                     : "l"((u64)map), "r"(0), "r"((int)(row0 + (u64)b)), "r"(s + (uint32_t)b * 128u)
-                     : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-// A thread's run of L values to the swizzled staging positions p0 .. p0 +
-// L - 1, in 16-byte chunks where the positions allow (p0 even), else as a
-// single first and last element around L / 2 - 1 chunks. p0 = my0 (the
-// unshifted staging) keeps the positions visible to the compiler.
-template <int L>
-__device__ __forceinline__ void stage_run(u64 *st, int my0, int shift, const u64 (&v)[L])
-{
-    if (shift == 0) {
-#pragma unroll
-        for (int k = 0; k < L / 2; k++)
-            *reinterpret_cast<ulonglong2 *>(st + swz(my0 + 2 * k)) =
-                make_ulonglong2(v[2 * k], v[2 * k + 1]);
-        return;
-    }
-    const int p0 = my0 + shift;
-    if ((p0 & 1) == 0) {
-#pragma unroll
-        for (int k = 0; k < L / 2; k++)
-            *reinterpret_cast<ulonglong2 *>(st + swz(p0 + 2 * k)) =
-                make_ulonglong2(v[2 * k], v[2 * k + 1]);
-    } else {
-        st[swz(p0)] = v[0];
-#pragma unroll
-        for (int k = 1; k < L / 2; k++)
-            *reinterpret_cast<ulonglong2 *>(st + swz(p0 + 2 * k - 1)) =
-                make_ulonglong2(v[2 * k - 1], v[2 * k]);
-        st[swz(p0 + L - 1)] = v[L - 1];
-    }
-}
-
-// Element stores of staged outputs i = t, t + T, ... below n from staging
-// position shift + i to dst[i * stride]. For T a multiple of 128 the
-// swizzled position of shift + t + kT is that of shift + t plus kT (the
-// line advances by a multiple of 8), so it is computed once.
-__device__ __forceinline__ void put(double *p, u64 bits) { *p = __longlong_as_double((long long)bits); }
-__device__ __forceinline__ void put(u64 *p, u64 bits) { *p = bits; }
-
-template <class V>
-__device__ __forceinline__ void store_elements(V *dst, const u64 *st, int n, int shift,
-                                               u64 stride)
-{
-    const int T = blockDim.x, t = threadIdx.x;
-    if ((T & 127) == 0) {
-        for (int i = t, j = swz(shift + t); i < n; i += T, j += T)
-            put(dst + (u64)i * stride, st[j]);
-    } else {
-        for (int i = t; i < n; i += T)
-            put(dst + (u64)i * stride, st[swz(shift + i)]);
-    }
-}
-
-// Waits until the bulk stores issued by this thread have read their source
-// (read = true) or have completed.
-template <bool READ>
-__device__ __forceinline__ void bulk_wait_all()
-{
-    if constexpr (READ)
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-    else
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // U < L: the encryption runs in passes of U chains (the unroll knob).
@@ -791,6 +700,11 @@ size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c)
     return (size_t)nbuf * stage_elements(threads * L, nbuf) * 8 *
                ((want_r ? 1 : 0) + (want_c ? 1 : 0)) +
            1024;
+}
+
+StoreMaps make_store_maps(const GenLaunch &g, int L, double *out_r, uint64_t *out_c)
+{
+    return store_maps(g, L, out_r, out_c);
 }
 
 size_t padded_smem_bytes(int threads, int L, bool want_r, bool want_c)
