@@ -59,6 +59,9 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
     const int K = TS * L;  // positions of each instance per tile
     const int S = K * G;   // = T L outputs per tile
     const int my0 = lt * L;
+    // 16-byte column-pair stores of the k-major rows (see below)
+    const bool pairs = !PACKED && G >= 2 && (stride & 1) == 0 &&
+                       ((uintptr_t)out_r & 15) == 0 && ((uintptr_t)out_c & 15) == 0;
     u64 *st_r = smem;
     u64 *st_c = smem + (out_r ? S + (S >> 4) : 0);
 
@@ -131,6 +134,35 @@ __global__ void __launch_bounds__(TB ? TB : 512, TB ? 5 : 1)
                             out_r[o + k] = __longlong_as_double((long long)st_r[slot]);
                         if (out_c)
                             out_c[o + k] = st_c[slot];
+                    }
+                }
+            } else if (pairs && (o0 & 1) == 0) {
+                // Written k-major in column pairs: thread t writes columns
+                // 2c and 2c + 1 (c = t mod G/2) of rows t / (G/2), ... with
+                // one 16-byte store per pair (even stride and first element,
+                // 16-byte aligned arrays); a pair whose second column lies
+                // past the group's streams stores its first alone.
+                const int c2 = 2 * (t & ((G >> 1) - 1));
+                const int r0 = t >> (gsh - 1), rstep = 2 * TS;
+                if (c2 < (int)V.count) {
+                    const bool two = c2 + 1 < (int)V.count;
+                    u64 e = o0 + (base + (u64)r0) * stride + (u64)c2;
+                    const u64 step = (u64)rstep * stride;
+                    for (int k = r0; k < tile_n; k += rstep, e += step) {
+                        const int a = sidx(c2 * K + k), b = sidx((c2 + 1) * K + k);
+                        if (two) {
+                            if (out_r)
+                                *reinterpret_cast<ulonglong2 *>(out_r + e) =
+                                    make_ulonglong2(st_r[a], st_r[b]);
+                            if (out_c)
+                                *reinterpret_cast<ulonglong2 *>(out_c + e) =
+                                    make_ulonglong2(st_c[a], st_c[b]);
+                        } else {
+                            if (out_r)
+                                out_r[e] = __longlong_as_double((long long)st_r[a]);
+                            if (out_c)
+                                out_c[e] = st_c[a];
+                        }
                     }
                 }
             } else if (wcol < (int)V.count) {
