@@ -599,15 +599,17 @@ def form_split_full(R, torch, device, pk, rank, slice_parents: int = 1024) -> di
     return out
 
 
-def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
+def form_served(R, torch, device, pk, rank,
+                loads=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)) -> dict:
     """Serving: 1e6 registered instances, Poisson arrivals, log-uniform counts in
-    [2^4, 2^24]; closed-loop capacity first, then open-loop replays at fractions of it."""
+    [2^4, 2^24], 10^4 requests per point; closed-loop capacity first, then open-loop
+    replays at fractions of it (overload included), each point the median of three."""
     cfg = workload.CONFIGS["serving_1e6"]
     k = cfg["instances"]
     ctx = R.Context(k, device=device)
     first = ctx.create_seeded(workload.instance_seeds(cfg["master"], k, first=rank * k),
                               cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
-    nreq = 4000
+    nreq = 10000
     pick = first + workload.uniform_indices(61, nreq, k)
     cnt = workload.loguniform_counts(62, nreq, lo=16, hi=1 << 24)
     # The library's default configuration: the autotuner's sample of the request mix
@@ -620,7 +622,7 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
     srv = R.Server(ctx, out_budget_bytes=16 << 30, nstreams=4)
     mean_cnt = float(cnt.mean())
     # capacity: all requests at once (arrival 0), the server batching freely; the median
-    # of three replays (one takes about 45 ms)
+    # of three replays (one takes about 0.1 s)
     caps = []
     for _ in range(3):
         srv.replay(pick, cnt, np.zeros(nreq), timeout_s=300)
@@ -644,14 +646,17 @@ def form_served(R, torch, device, pk, rank, loads=(0.25, 0.5, 0.9)) -> dict:
                        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                        "p99_ms_of_replays": [round(s["p99_ms"], 3) for s in runs],
                        "iterations": st["iterations"],
-                       "overlapped_iterations": st["overlapped_iterations"]})
+                       "overlapped_iterations": st["overlapped_iterations"],
+                       "submitted": st["submitted"], "admitted": st["admitted"],
+                       "completed": st["completed"], "rejected": st["rejected"],
+                       "max_inflight_iterations": st["max_inflight_iterations"]})
     es = [ctx.params(int(i))[2] for i in pick[:200]]
     mean_slots = float(np.mean([imad_slots_per_number(int(e)) for e in es]))
     divide = ctx.config()["divide"]
     srv.close()
     ctx.close()
     torch.cuda.empty_cache()
-    mid = points[len(points) // 2]
+    mid = next((pt for pt in points if pt["load"] == 0.5), points[len(points) // 2])
     return {"value": round(cap_numbers / 1e9, 3), "unit": UNIT,
             "capacity_req_per_s": round(cap_rate, 1), "requests_per_point": nreq,
             "capacity_of_replays": [round(x / 1e9, 3) for x in caps],
