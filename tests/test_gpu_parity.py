@@ -590,13 +590,14 @@ def test_microbenchmarks_run():
     assert ctx.microbench(2, 1 << 30) > 500.0  # GB/s
 
 
-def test_bulk_full_size_sampled(O):
-    """Plain bulk at full size (1024 instances x 2^20 float64, one instance per block, 8 GiB)
-    in the launch configuration the benchmark times; 8 instances compared in full, every
-    instance at sampled indices, and every end state."""
+def test_bulk_full_size_all_outputs(O):
+    """Plain bulk at full size (1024 instances x 2^20 float64, 8 GiB) in the launch
+    configuration the benchmark times (whole streams, four pieces per resident block, bulk
+    tensor stores): all 2^30 outputs compared with the oracle's direct route, 128 instances
+    at a time, and every end state."""
     cfg = workload.CONFIGS["bulk_1024x2^20"]
     k, n = cfg["instances"], cfg["count"]
-    ctx = R.Context(k, chunk=n)
+    ctx = R.Context(k, chunk=n, pieces_per_block=4)
     seeds = workload.instance_seeds(cfg["master"], k)
     first = ctx.create_seeded(seeds, cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
     ids = np.arange(first, first + k, dtype=np.uint32)
@@ -608,20 +609,17 @@ def test_bulk_full_size_sampled(O):
     p = np.array([x[0] for x in par], np.uint64)
     q = np.array([x[1] for x in par], np.uint64)
     e = np.array([x[2] for x in par], np.uint64)
-    m0 = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
-    rng = np.random.default_rng(5)
-    ks = [np.unique(np.concatenate([[1, 2, n], rng.integers(1, n + 1, 29)])) for _ in range(k)]
-    m = m0.copy()
+    m = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
     s = np.ones(k, np.uint64)
-    _, want_r = O.sample_many(p, q, e, np.full(k, A, np.uint64), m, s, ks)
-    idx = np.concatenate([i * n + kk - 1 for i, kk in enumerate(ks)]).astype(np.int64)
-    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
-    assert np.array_equal(bits(got), bits(want_r))
-    # end state of every instance = oracle after n outputs (m, s were advanced to k = n)
-    for i in range(k):
-        assert ctx.get_state(int(ids[i])) == (int(m[i]), int(s[i])), i
-    full = [0, 1, 511, 1023, 100, 200, 300, 400]
-    g = out.view(k, n)[full].cpu().numpy()
-    for j, i in enumerate(full):
-        check_stream(O, par[i][:3], int(m0[i]), 1, None, g[j])
+    B = 128
+    for i0 in range(0, k, B):
+        sl = slice(i0, i0 + B)
+        mm, ss = m[sl].copy(), s[sl].copy()
+        _, want = O.generate_many(p[sl], q[sl], e[sl], np.full(B, A, np.uint64), mm, ss,
+                                  np.full(B, n, np.uint64), route=O.ROUTE_DIRECT, want_c=False)
+        got = out[i0 * n:(i0 + B) * n].cpu().numpy()
+        bad = np.nonzero(bits(got) != bits(want))[0]
+        assert len(bad) == 0, f"instances {i0}..: {len(bad)} outputs differ, first {bad[:3]}"
+        for j in range(B):
+            assert ctx.get_state(int(ids[i0 + j])) == (int(mm[j]), int(ss[j])), i0 + j
     plan.close()
