@@ -702,11 +702,6 @@ size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c)
            1024;
 }
 
-StoreMaps make_store_maps(const GenLaunch &g, int L, double *out_r, uint64_t *out_c)
-{
-    return store_maps(g, L, out_r, out_c);
-}
-
 size_t padded_smem_bytes(int threads, int L, bool want_r, bool want_c)
 {
     const size_t S = (size_t)threads * L;

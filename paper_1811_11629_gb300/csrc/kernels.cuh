@@ -87,12 +87,9 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 // buffers (gen_stage_buffers per output kind) and 1 KB to align them.
 size_t gen_smem_bytes(int threads, int L, bool want_r, bool want_c);
 int gen_stage_buffers(int threads, int L, bool want_r, bool want_c);
-// The padded staging of the vector kernel: one 8-byte pad slot every 16
-// elements, per output kind.
+// The padded staging of the vector and single-launch kernels: one 8-byte pad
+// slot every 16 elements, per output kind.
 size_t padded_smem_bytes(int threads, int L, bool want_r, bool want_c);
-// The bulk-store views of a launch's output arrays (extent 0 when the arrays
-// or the launch do not allow bulk stores: see k_generate).
-StoreMaps make_store_maps(const GenLaunch &g, int L, double *out_r, uint64_t *out_c);
 
 size_t vec_smem_bytes(int threads, int L, bool want_r, bool want_c);
 // Numbers per thread the vector kernel uses for a configured L: the tuned

@@ -39,6 +39,7 @@ namespace {
 using dev::addmod;
 using dev::mulmodQ;
 using tile::FULL;
+using tile::sidx;
 using tile::to_unit;
 
 // Per-tile status: the tile aggregate and the inclusive prefix, each with the
@@ -145,18 +146,10 @@ __device__ __forceinline__ bool block_lookback(const LbStatus *st, uint32_t b, u
     return true;
 }
 
-// Shared memory of a single-launch block: one swizzled staging buffer per
-// output kind, and 1 KB to align it.
-size_t lb_smem_bytes(int threads, int L, bool want_r, bool want_c)
-{
-    return (size_t)threads * L * 8 * ((want_r ? 1 : 0) + (want_c ? 1 : 0)) + 1024;
-}
-
 template <int L, int MODEXP, int DIV>
 __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbArgs A,
                                                          double *__restrict__ out_r,
-                                                         u64 *__restrict__ out_c,
-                                                         const __grid_constant__ StoreMaps maps)
+                                                         u64 *__restrict__ out_c)
 {
     extern __shared__ u64 smem[];
     __shared__ u64 sh_scan[32];
@@ -165,11 +158,9 @@ __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbA
     __shared__ int sh_near;
     const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
     const int S = T * L;
-    // one staging buffer per output kind in the 128-byte-swizzled layout of
-    // the bulk stores, 1024-byte aligned
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    u64 *const st_r = smem + (((sbase + 1023u) & ~1023u) - sbase) / 8;
-    u64 *const st_c = st_r + (out_r ? S : 0);
+    const int slots = S + (S >> 4);
+    u64 *st_r = smem;
+    u64 *st_c = smem + (out_r ? slots : 0);
     if (t == 0) {
         // Logical tile in start order; the instance state is read before
         // anything is published, so the block that writes the new state
@@ -246,46 +237,32 @@ __global__ void __launch_bounds__(512) k_generate_lookback(DeviceTables tab, LbA
                                            total);
     if (failed)
         return;
-    // Output: a whole tile leaves by bulk tensor stores (its first output,
-    // bS, is a multiple of 16 elements), the ragged last tile by element
-    // stores; the issuing thread waits for its copies before the block ends.
-    if (out_r) {
 #pragma unroll
-        for (int q = 0; q < L / 2; q++)
-            *reinterpret_cast<ulonglong2 *>(st_r + tile::swz(my0 + 2 * q)) = make_ulonglong2(
-                (u64)__double_as_longlong(to_unit<DIV>(c[2 * q], P, 2 * q)),
-                (u64)__double_as_longlong(to_unit<DIV>(c[2 * q + 1], P, 2 * q + 1)));
-    }
-    if (out_c)
-        tile::stage_run<L>(st_c, my0, 0, c);
-    const bool bulk = maps.extent && tile_n == S && base + (u64)S <= maps.extent;
-    if (bulk)
-        tile::fence_async_shared();
-    __syncthreads();
-    if (bulk) {
-        if (t == 0) {
-            if (out_r)
-                tile::bulk_store_rows(&maps.r, st_r, S >> 4, maps.box_rows, base >> 4);
-            if (out_c)
-                tile::bulk_store_rows(&maps.c, st_c, S >> 4, maps.box_rows, base >> 4);
-        }
-    } else {
+    for (int j = 0; j < L; j++) {
+        const int i = sidx(my0 + j);
         if (out_r)
-            tile::store_elements(out_r + base, st_r, tile_n, 0, 1);
+            st_r[i] = (u64)__double_as_longlong(to_unit<DIV>(c[j], P, j));
         if (out_c)
-            tile::store_elements(out_c + base, st_c, tile_n, 0, 1);
+            st_c[i] = c[j];
+    }
+    __syncthreads();
+    if (out_r) {
+        for (int i = t; i < tile_n; i += T)
+            out_r[base + i] = __longlong_as_double((long long)st_r[sidx(i)]);
+    }
+    if (out_c) {
+        for (int i = t; i < tile_n; i += T)
+            out_c[base + i] = st_c[sidx(i)];
     }
     if ((W.flags & WI_WRITEBACK) && t == 0)
         tab.state_m[A.inst] = addmod(addmod(sh_m0, carry, P.n), total, P.n);
-    if (bulk && t == 0)
-        tile::bulk_wait_all<false>();
 }
 
 template <int L, int MODEXP, int DIV>
 cudaError_t launch_lb_t(int threads, const DeviceTables &tab, const LbArgs &A, double *out_r,
                         u64 *out_c, cudaStream_t stream)
 {
-    const size_t smem = lb_smem_bytes(threads, L, out_r != nullptr, out_c != nullptr);
+    const size_t smem = padded_smem_bytes(threads, L, out_r != nullptr, out_c != nullptr);
     auto kern = k_generate_lookback<L, MODEXP, DIV>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -293,13 +270,7 @@ cudaError_t launch_lb_t(int threads, const DeviceTables &tab, const LbArgs &A, d
         if (e != cudaSuccess)
             return e;
     }
-    GenLaunch g{};
-    g.threads = threads;
-    g.L = L;
-    g.stride = 1;
-    g.out_extent = A.N;
-    const StoreMaps maps = make_store_maps(g, L, out_r, out_c);
-    kern<<<A.ntiles, threads, smem, stream>>>(tab, A, out_r, out_c, maps);
+    kern<<<A.ntiles, threads, smem, stream>>>(tab, A, out_r, out_c);
     return cudaGetLastError();
 }
 
@@ -336,7 +307,7 @@ int latency_occupancy(bool exact, bool both)
     if (o < 0) {
         const void *k = exact ? (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_EXACT>
                               : (const void *)k_generate_lookback<16, MODEXP_CRT32, DIVIDE_INT>;
-        const size_t smem = lb_smem_bytes(512, 16, true, both);
+        const size_t smem = padded_smem_bytes(512, 16, true, both);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int b = 0;
