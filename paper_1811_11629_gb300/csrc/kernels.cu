@@ -399,8 +399,9 @@ bool encode_view(CUtensorMap *m, void *base, uint64_t rows, int box_rows)
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Whether p is (null or) device memory: page-locked host memory that the
-// kernel writes through its mapping keeps the element stores.
+// Whether p is (null or) memory of the current device: page-locked host
+// memory that the kernel writes through its mapping, and another device's
+// memory, keep the element stores.
 bool device_or_null(const void *p)
 {
     if (!p)
@@ -416,7 +417,9 @@ bool device_or_null(const void *p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // The store maps of a launch: bulk stores need the contiguous order, a known
