@@ -342,6 +342,48 @@ def cpu_baseline(cfg: dict, seeds: np.ndarray, target_s: float = 10.0) -> dict:
                       f"route=paper (Schrage + CRT), {dt:.1f} s wall"}
 
 
+def cpu_oracle_form(name: str, target_s: float = 3.0) -> dict:
+    """The oracle (paper route) on a bounded sample of a form's own workload, timed on the
+    host cores beside the GPU figure: plain (its one instance, the whole 1e6-number call,
+    u64 + f64, one core), batched (its first 2000 instances) and the split workload (4096
+    parents x 2^16 numbers; substreams differ from their parent only in the skip state, so
+    the parents stand for them)."""
+    import oracle
+
+    oracle.build()
+    key = {"plain_1x1e6": "plain_1x1e6", "batched_1e5_lognormal": "batched_1e5_lognormal",
+           "split_interleaved": "split_65536x32x2^16"}[name]
+    cfg = workload.CONFIGS[key]
+    k = {"plain_1x1e6": 1, "batched_1e5_lognormal": 2000, "split_interleaved": 4096}[name]
+    cap = cfg["count"] if name != "batched_1e5_lognormal" else 1 << 30
+    both = name != "batched_1e5_lognormal"
+    seeds = workload.instance_seeds(cfg["master"], k)
+    par = [oracle.params_from_seed(int(s), cfg["e_rule"], cfg["e_lo"], cfg["e_hi"])
+           for s in seeds]
+    p = np.array([x[0] for x in par], np.uint64)
+    q = np.array([x[1] for x in par], np.uint64)
+    e = np.array([x[2] for x in par], np.uint64)
+    a = np.full(k, 2307085864, np.uint64)
+
+    def run(n):
+        m = np.array([x[3] % (x[0] * x[1]) for x in par], np.uint64)
+        s = np.ones(k, np.uint64)
+        t0 = time.perf_counter()
+        oracle.generate_many(p, q, e, a, m, s, np.full(k, n, np.uint64),
+                             route=oracle.ROUTE_PAPER, want_c=both, want_r=True)
+        return time.perf_counter() - t0
+
+    pilot = 8192
+    dt = run(pilot)
+    n = int(min(cap, max(pilot, pilot * target_s / max(dt, 1e-3))))
+    dt = run(n)
+    cores = 1 if k == 1 else min(k, oracle.max_threads())
+    return {"value": round(k * n / dt / 1e9, 5), "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{k} instance(s) of the workload x {n} numbers each"
+                      f"{' (u64 + f64)' if both else ''}, route=paper, {dt:.2f} s wall"}
+
+
 # --------------------------------------------------------------------------- other forms
 TUNED_KEYS = ("modexp", "divide", "threads_per_block", "numbers_per_thread", "blocks_per_sm",
               "chunk", "streams_per_block", "unroll", "pieces_per_block")
@@ -844,6 +886,10 @@ def run_ours(args) -> int:
                 ("split_full_65536x32x2^16", "split_full",
                  lambda: form_split_full(R, torch, lr, pk, rk)))
         result["forms"] = {name: fn() for name, key, fn in runs if key in want}
+        if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+            for name in ("plain_1x1e6", "batched_1e5_lognormal", "split_interleaved"):
+                if name in result["forms"]:
+                    result["forms"][name]["cpu_oracle"] = cpu_oracle_form(name)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cfg, seeds)
     if args.tune_cache:

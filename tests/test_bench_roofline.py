@@ -60,3 +60,14 @@ def test_bounds_pick_the_binding_unit():
     assert abs(f["fp64_frac"] - 10 * (1 / 70 + 1 / 300)) < 1e-4
     # nothing stored: no HBM work
     assert f["hbm_frac"] == 0.0
+
+
+def test_cpu_oracle_forms():
+    """The oracle timed beside the plain, batched and split forms: a positive rate on a
+    bounded sample of each form's own workload, with the cores it used."""
+    for name, k in (("plain_1x1e6", 1), ("batched_1e5_lognormal", 2000),
+                    ("split_interleaved", 4096)):
+        r = bench.cpu_oracle_form(name, target_s=0.05)
+        assert r["kind"] == "oracle" and r["unit"] == bench.UNIT and r["value"] > 0
+        assert r["cores"] == (1 if k == 1 else min(k, oracle.max_threads()))
+        assert r["sample"].startswith(f"{k} instance")
