@@ -140,3 +140,32 @@ def test_many_vectors_in_one_call(O):
         want, _ = O.generate_vector(full(p), full(q), full(e), full(A),
                                     full(ms % (p * q)), s0, N)
         np.testing.assert_array_equal(got[g], want)
+
+
+@pytest.mark.parametrize("shift_r,shift_c", [(1, 1), (1, 0), (0, 1)])
+def test_interleaved_unaligned_outputs(O, shift_r, shift_c):
+    """Arrays that start 8 bytes past a 16-byte boundary take the one-column
+    stores instead of the column-pair ones; the words around the written span
+    stay as they were."""
+    ctx = R.Context(16, threads_per_block=128, numbers_per_thread=8)
+    seed = workload.instance_seeds(68, 1)
+    parent = ctx.create_seeded(seed, R.E_UNIFORM, 3, 257)
+    p, q, e, ms = O.params_from_seed(int(seed[0]), R.E_UNIFORM, 3, 257)
+    Mv, N = 8, 5003
+    kids = ctx.split(parent, Mv)
+    n = N * Mv
+    br = torch.full((n + 2,), -1.0, dtype=torch.float64, device="cuda")
+    bc = torch.full((n + 2,), -7, dtype=torch.int64, device="cuda")
+    r, c = br[shift_r:shift_r + n], bc[shift_c:shift_c + n]
+    assert (r.data_ptr() % 16 == 8) == bool(shift_r) and (c.data_ptr() % 16 == 8) == bool(shift_c)
+    ctx.generate_interleaved(kids, N, out_r=r, out_c=c)
+    torch.cuda.synchronize()
+    full = lambda x: np.full(Mv, x, np.uint64)
+    s0 = np.array([O.split_s0(1, A, Mv, g) for g in range(Mv)], np.uint64)
+    want_c, want_r = O.generate_vector(full(p), full(q), full(e), full(A), full(ms % (p * q)), s0, N)
+    np.testing.assert_array_equal(c.cpu().numpy().view(np.uint64), want_c)
+    assert (bits(r.cpu().numpy()) == bits(want_r)).all()
+    hr, hc = br.cpu().numpy(), bc.cpu().numpy()
+    outside_r = np.r_[hr[:shift_r], hr[shift_r + n:]]
+    outside_c = np.r_[hc[:shift_c], hc[shift_c + n:]]
+    assert (outside_r == -1.0).all() and (outside_c == -7).all()
