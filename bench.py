@@ -418,16 +418,18 @@ def form_plain(R, torch, device, pk, rank) -> dict:
     dt = sorted(groups)[len(groups) // 2]
     e = ctx.params(first)[2]
     divide = ctx.config()["divide"]
-    # A 1e6 draw fits one wave of the latency shape: 512 x 16 tiles, integer division.
+    # A 1e6 draw fits one wave of 512 x 16 tiles, so it runs in a latency shape: at most
+    # one tile per SM, 12-16 outputs per thread (512 x 13 on 152 SMs), integer division.
     out = {"value": round(n / dt / 1e9, 3), "unit": UNIT, "ms_per_call": round(dt * 1e3, 4),
            "ms_per_call_of_groups": [round(g * 1e3, 4) for g in groups],
            "e": e, "outputs": "u64+f64", "divide": DIVIDE_INT,
            "hbm_GBps": round(16 * n / dt / 1e9, 1)}
     out.update(bounds(pk, n, _slots([e], [n]), dt, DIVIDE_INT, 16))
     out["path"] = ("one launch, decoupled look-back over the tiles' skip sums, latency shape "
-                   "(512 x 16 tiles, integer division)")
-    # One wave of 123 blocks, each a short chain of dependent phases: no pipe is the limit
-    # (ncu: issue 38 % active, fetch and barrier stalls); the fractions above say how far.
+                   "(at most one tile per SM, 12-16 outputs per thread, integer division)")
+    # One wave of at most one block per SM, each a short chain of dependent phases: no pipe
+    # is the limit (ncu: issue 38 % active, fetch and barrier stalls); the fractions above
+    # say how far.
     out["limited_by"] = "latency (one wave; no pipe saturated)"
     # The same calls through the chunked path (skip-sum pre-pass, scan, generation).
     ctx.configure(lookback=R.LOOKBACK_OFF)

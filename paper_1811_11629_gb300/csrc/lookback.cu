@@ -24,6 +24,7 @@
 //
 // Status words carry the call's epoch (a per-context counter, never reused),
 // so the status array needs no clearing between calls.
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -285,6 +286,9 @@ cudaError_t launch_lookback(int L, int modexp, int divide, int threads, const De
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_RECIP)
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_HYBRID)
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_LB(14, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_LB(13, MODEXP_CRT32, DIVIDE_INT)
+    RSAPRNG_LB(12, MODEXP_CRT32, DIVIDE_INT)
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_FP64)
     RSAPRNG_LB(16, MODEXP_CRT32, DIVIDE_EXACT)
     RSAPRNG_LB(8, MODEXP_CRT32, DIVIDE_RECIP)
@@ -318,6 +322,42 @@ int latency_occupancy(bool exact, bool both)
     return o;
 }
 
+
+// The tile shape of a latency-mode draw of N outputs on sms SMs: threads (a
+// multiple of 32, 128 to 512) and outputs per thread L, with at most one tile
+// per SM. The four warp schedulers of an SM then share the tile's warps, so
+// a scheduler issues the work of ceil(threads / 128) warps of L outputs each
+// while every warp runs a chain of L dependent outputs. Of the shapes whose
+// tiles cover the draw on one tile per SM, the one that minimises
+// L (max(w, 2) + 1), w = ceil(threads / 128), is taken (smaller L on a tie):
+// a fit to the measured call time, which grows with the per-scheduler work
+// w L and with the chain length L, and which one warp per scheduler does not
+// hide. The exact-rational route has only L = 16. When no shape covers the
+// draw on one tile per SM, 512 x 16.
+void latency_shape(uint64_t N, int sms, bool exact, int *threads, int *L)
+{
+    static const int kLs[] = {12, 13, 14, 16};
+    *threads = 512;
+    *L = 16;
+    uint64_t best = UINT64_MAX;
+    for (int Lc : kLs) {
+        if (exact && Lc != 16)
+            continue;
+        const uint64_t per = (uint64_t)Lc * (uint64_t)sms;
+        uint64_t T = ((N + per - 1) / per + 31) / 32 * 32;
+        if (T < 128)
+            T = 128;
+        if (T > 512)
+            continue;
+        const uint64_t w = (T + 127) / 128;
+        const uint64_t cost = (uint64_t)Lc * ((w < 2 ? 2 : w) + 1);
+        if (cost < best) {
+            best = cost;
+            *threads = (int)T;
+            *L = Lc;
+        }
+    }
+}
 
 // Tiles of one single-launch call at most (the status array of a scratch
 // slot holds this many); longer draws take the chunked path.
@@ -353,19 +393,19 @@ int generate_single_launch(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *
         return fail(RSAPRNG_ERR_ARG, "instance %u has CRT exponents: the 64-bit route cannot "
                                      "run it", id);
     // Latency mode. A draw that fits one wave of 512-thread blocks of 16
-    // outputs per thread runs in that shape, on the CRT route with the
-    // integer division. Every block then starts at once and runs the same
-    // phases at the same time, so the phases add up rather than overlap. The
-    // integer division keeps the division phase off the two-lane FP64 pipe,
-    // and the few large tiles keep the look-back short. All shapes and routes
-    // give the same bits; larger draws keep the configured (throughput) shape.
+    // outputs per thread runs in a latency shape (latency_shape), on the CRT
+    // route with the integer division. Every block then starts at once and
+    // runs the same phases at the same time, so the phases add up rather than
+    // overlap. The integer division keeps the division phase off the two-lane
+    // FP64 pipe, and one tile per SM at most keeps the look-back short. All
+    // shapes and routes give the same bits; larger draws keep the configured
+    // (throughput) shape.
     if (cfg.lookback != RSAPRNG_LOOKBACK_CONFIGURED) {
         const bool exact = cfg.rounding == RSAPRNG_ROUND_EXACT;
         const uint64_t S_lat = 512 * 16;
         const uint64_t wave = (uint64_t)latency_occupancy(exact, d_r && d_c) * c->sms;
         if ((N + S_lat - 1) / S_lat <= wave) {
-            g.threads = 512;
-            g.L = 16;
+            latency_shape(N, c->sms, exact, &g.threads, &g.L);
             g.modexp = MODEXP_CRT32;
             g.divide = exact ? DIVIDE_EXACT : DIVIDE_INT;
         }

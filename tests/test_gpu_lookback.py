@@ -84,16 +84,41 @@ def test_single_launch_sizes_against_oracle(O, cfg):
     assert ctx.device_status() == 0
 
 
+def _latency_shape(n, sms, exact):
+    """The latency-mode tile (threads, outputs per thread) for a draw of n, restated
+    from the library's rule so that the sizes below land on its tile boundaries:
+    one tile per SM at most, the least L (max(w, 2) + 1) with w = ceil(threads / 128)."""
+    best, shape = None, (512, 16)
+    for L in ((16,) if exact else (12, 13, 14, 16)):
+        T = -(-n // (L * sms))          # threads for one tile per SM
+        T = max(128, -(-T // 32) * 32)  # whole warps, 128 at least
+        if T > 512:
+            continue
+        cost = L * (max(-(-T // 128), 2) + 1)
+        if best is None or cost < best:
+            best, shape = cost, (T, L)
+    return shape
+
+
 @pytest.mark.parametrize("rounding", [0, 2])
 def test_latency_shape_sizes_against_oracle(O, rounding):
-    """The latency shape (512 x 16, CRT, integer division) for draws that fit one wave,
-    around its tiles and the wave's end, then the configured shape beyond it."""
+    """The latency shapes (tiles of 128-512 threads x 12-16 outputs, at most one per
+    SM; CRT, integer division) for draws that fit one wave of 512 x 16 tiles: around
+    the chosen tiles' ends and the wave's end, then the configured shape beyond it."""
     ctx = R.Context(4, rounding=rounding)
     i, (p, q, e, m0) = _instance(ctx, O, 74)
     S = 512 * 16
     m, s = m0, 1
     sm = torch.cuda.get_device_properties(0).multi_processor_count
-    for n in (1, S - 1, S, S + 1, 1_000_000, sm * S, sm * S + 1):
+    sizes = [1, S - 1, S, S + 1, 1_000_000, sm * S, sm * S + 1]
+    shapes = set()
+    for probe in (100_000, 300_000, 600_000, 800_000, 1_000_000, 1_100_000):
+        T, L = _latency_shape(probe, sm, rounding == 2)
+        shapes.add(L)
+        k = -(-probe // (T * L))
+        sizes += [k * T * L - 1, k * T * L, k * T * L + 1]
+    assert rounding == 2 or shapes >= {12, 13, 14, 16} or sm != 152
+    for n in sizes:
         launches = ctx.launches
         c, r = _draw(ctx, i, n)
         assert ctx.launches - launches == 1
