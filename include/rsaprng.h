@@ -243,6 +243,18 @@ int rsaprng_generate_f64(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, double *d_
 int rsaprng_generate_both(rsaprng_ctx *ctx, rsaprng_id id, uint64_t N, uint64_t *d_c, double *d_r,
                           void *stream);
 
+/* The tile shape of the single launch above for a draw of N outputs on a GPU
+ * with `sms` SMs, when the draw fits one wave of 512 x 16 tiles (the latency
+ * mode; larger draws, and contexts configured with RSAPRNG_LOOKBACK_CONFIGURED,
+ * use the configured tiling). Writes the threads per block (a multiple of 32,
+ * 128 to 512) and the outputs per thread (12, 13, 14 or 16; 16 only when
+ * rounding_exact is nonzero), with at most one tile per SM where such a shape
+ * covers N. The paper has no counterpart: it is the launch geometry of this
+ * implementation, a pure host function (no GPU, no context). Returns
+ * RSAPRNG_ERR_ARG for a null output pointer or sms < 1. */
+int rsaprng_latency_shape(uint64_t N, int sms, int rounding_exact, int *threads,
+                          int *numbers_per_thread);
+
 /* The same as rsaprng_generate_f64, for callers that cannot allocate device
  * memory when they draw numbers: latency-critical threads that forbid
  * allocator calls, or hosts that give all device memory to their own pool.

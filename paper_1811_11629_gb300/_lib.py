@@ -75,6 +75,7 @@ SIGNATURES = {
     "rsaprng_generate_f64": (i32, [vp, u32, u64, vp, vp]),
     "rsaprng_generate_both": (i32, [vp, u32, u64, vp, vp, vp]),
     "rsaprng_generate_f64_noalloc": (i32, [vp, u32, u64, vp, vp]),
+    "rsaprng_latency_shape": (i32, [u64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     "rsaprng_generate_batch": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_generate_batch_host": (i32, [vp, u64, pu32, pu64, pu64, vp, vp, vp]),
     "rsaprng_histogram": (i32, [vp, u64, pu32, pu64, u32, u32, i32, vp, vp]),

@@ -468,6 +468,16 @@ int generate_single_launch(rsaprng_ctx *c, rsaprng_id id, uint64_t N, uint64_t *
 
 }  // namespace rsaprng
 
+extern "C" int rsaprng_latency_shape(uint64_t N, int sms, int rounding_exact, int *threads,
+                                     int *numbers_per_thread)
+{
+    using namespace rsaprng;
+    if (!threads || !numbers_per_thread || sms < 1)
+        return fail(RSAPRNG_ERR_ARG, "latency_shape: null output or sms < 1");
+    latency_shape(N, sms, rounding_exact != 0, threads, numbers_per_thread);
+    return RSAPRNG_OK;
+}
+
 extern "C" int rsaprng_device_status(rsaprng_ctx *c, void *stream)
 {
     using namespace rsaprng;

@@ -9,6 +9,8 @@ context's device error flag (the waits are bounded), leave the context usable,
 and fault nothing: the test makes tile 0 publish nothing, so that every later
 tile's wait runs out.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -85,19 +87,11 @@ def test_single_launch_sizes_against_oracle(O, cfg):
 
 
 def _latency_shape(n, sms, exact):
-    """The latency-mode tile (threads, outputs per thread) for a draw of n, restated
-    from the library's rule so that the sizes below land on its tile boundaries:
-    one tile per SM at most, the least L (max(w, 2) + 1) with w = ceil(threads / 128)."""
-    best, shape = None, (512, 16)
-    for L in ((16,) if exact else (12, 13, 14, 16)):
-        T = -(-n // (L * sms))          # threads for one tile per SM
-        T = max(128, -(-T // 32) * 32)  # whole warps, 128 at least
-        if T > 512:
-            continue
-        cost = L * (max(-(-T // 128), 2) + 1)
-        if best is None or cost < best:
-            best, shape = cost, (T, L)
-    return shape
+    """The library's latency-mode tile (threads, outputs per thread) for a draw of n."""
+    T, L = ctypes.c_int32(), ctypes.c_int32()
+    assert R._lib.load().rsaprng_latency_shape(n, sms, int(exact), ctypes.byref(T),
+                                               ctypes.byref(L)) == 0
+    return T.value, L.value
 
 
 @pytest.mark.parametrize("rounding", [0, 2])

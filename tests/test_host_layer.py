@@ -133,3 +133,41 @@ def test_autotune_cache_file_round_trip(R, tmp_path):
     assert L.rsaprng_autotune_cache_size() == 2
     L.rsaprng_autotune_cache_clear()
     assert L.rsaprng_autotune_cache_size() == 0
+
+
+def _latency_shape(R, n, sms, exact):
+    L = R._lib.load()
+    T, per = ctypes.c_int32(), ctypes.c_int32()
+    assert L.rsaprng_latency_shape(n, sms, int(exact), ctypes.byref(T), ctypes.byref(per)) == 0
+    return T.value, per.value
+
+
+def test_latency_shape_rule(R):
+    """The single-launch plain call's tile for draws that fit one wave of 512 x 16
+    tiles: whole warps, 128 to 512 threads, 12-16 outputs per thread, at most one
+    tile per SM, and of those the least per-scheduler work plus chain length,
+    L (max(ceil(T / 128), 2) + 1), smaller L on a tie (checked against every
+    admissible shape)."""
+    for sms in (148, 152, 160):
+        for n in (1, 1000, 8191, 8192, 100_000, 300_000, 600_000, 800_000, 1_000_000,
+                  1_100_000, 8192 * sms - 1, 8192 * sms):
+            for exact in (False, True):
+                T, L = _latency_shape(R, n, sms, exact)
+                assert T % 32 == 0 and 128 <= T <= 512
+                assert L == 16 if exact else L in (12, 13, 14, 16)
+                assert -(-n // (T * L)) <= sms  # at most one tile per SM
+                cost = lambda t, l: l * (max(-(-t // 128), 2) + 1)
+                for l2 in ((16,) if exact else (12, 13, 14, 16)):
+                    for t2 in range(128, 513, 32):
+                        if -(-n // (t2 * l2)) <= sms:
+                            assert (cost(T, L), L) <= (cost(t2, l2), l2), (n, sms, T, L, t2, l2)
+                # the fewest threads for that L that still keep one tile per SM
+                assert T == 128 or -(-n // ((T - 32) * L)) > sms
+    # the shapes measured on 152 SMs
+    assert _latency_shape(R, 1_000_000, 152, False) == (512, 13)
+    assert _latency_shape(R, 800_000, 152, False) == (384, 14)
+    assert _latency_shape(R, 300_000, 152, False) == (192, 12)
+    L = R._lib.load()
+    x = ctypes.c_int32()
+    assert L.rsaprng_latency_shape(10, 0, 0, ctypes.byref(x), ctypes.byref(x)) != 0
+    assert L.rsaprng_latency_shape(10, 152, 0, None, ctypes.byref(x)) != 0
