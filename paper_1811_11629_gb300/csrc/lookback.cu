@@ -344,7 +344,10 @@ void latency_shape(uint64_t N, int sms, bool exact, int *threads, int *L)
         if (exact && Lc != 16)
             continue;
         const uint64_t per = (uint64_t)Lc * (uint64_t)sms;
-        uint64_t T = ((N + per - 1) / per + 31) / 32 * 32;
+        const uint64_t q = N / per + (N % per != 0);  // threads for one tile per SM
+        if (q > 512)
+            continue;
+        uint64_t T = (q + 31) / 32 * 32;
         if (T < 128)
             T = 128;
         if (T > 512)

@@ -167,6 +167,9 @@ def test_latency_shape_rule(R):
     assert _latency_shape(R, 1_000_000, 152, False) == (512, 13)
     assert _latency_shape(R, 800_000, 152, False) == (384, 14)
     assert _latency_shape(R, 300_000, 152, False) == (192, 12)
+    # a draw no shape covers on one tile per SM (up to the largest count) gets 512 x 16
+    assert _latency_shape(R, 2**64 - 1, 152, False) == (512, 16)
+    assert _latency_shape(R, 8192 * 152 + 1, 152, True) == (512, 16)
     L = R._lib.load()
     x = ctypes.c_int32()
     assert L.rsaprng_latency_shape(10, 0, 0, ctypes.byref(x), ctypes.byref(x)) != 0
