@@ -21,6 +21,7 @@ data-path collective); timing is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -427,6 +428,10 @@ def form_plain(R, torch, device, pk, rank) -> dict:
     out.update(bounds(pk, n, _slots([e], [n]), dt, DIVIDE_INT, 16))
     out["path"] = ("one launch, decoupled look-back over the tiles' skip sums, latency shape "
                    "(at most one tile per SM, 12-16 outputs per thread, integer division)")
+    T, per = ctypes.c_int32(), ctypes.c_int32()
+    if ctx.L.rsaprng_latency_shape(n, pk["sms"], 0, ctypes.byref(T), ctypes.byref(per)) == 0:
+        out["tile"] = {"threads": T.value, "per_thread": per.value,
+                       "tiles": -(-n // (T.value * per.value))}
     # One wave of at most one block per SM, each a short chain of dependent phases: no pipe
     # is the limit (ncu: issue 38 % active, fetch and barrier stalls); the fractions above
     # say how far.
